@@ -1,0 +1,241 @@
+"""FP64 CPU oracle for the linear-splatting rasterizer.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the package smoke check and
+by the benchmark's CPU-baseline leg, never by the product path.  It shares no
+code with the CUDA implementation; both read the same seeded inputs.
+
+Functions follow the paper's definitions (Sec. 3.1 Eq. 1-6, Sec. 3.2 Eq. 7-11,
+Sec. 3.3 Eq. 12-14, Appendix B Eq. 19-26); the readings where the paper is
+silent are listed at the top of lso.cpp.  Parity is pinned by tests in
+tests/test_oracle_*.py (closed forms, brute force, invariants, finite
+differences); the anti-aliasing compensation constants are parity unpinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lso.cpp")
+_LIB = os.path.join(_HERE, "liblso.so")
+_lib = None
+
+NP = 16
+P_MX, P_MY, P_A, P_B, P_C, P_O, P_RHO2, P_DEPTH, P_R, P_G, P_BL, P_EX, P_EY, P_SXX, P_SXY, P_SYY = range(16)
+
+DEFAULTS = dict(lam=2.5, kernel=0, ags=0, antialias=0, eps2d=0.3, alpha_min=1.0 / 255.0, alpha_max=0.999,
+                t_min=1e-4, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0), near=0.2, far=1e4, sh_degree=0)
+
+
+def build(force=False):
+    """Compile liblso.so with g++ (-ffp-contract=off keeps the binary32 tile
+    rule free of fused multiply-adds on every host)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.lso_project.restype = ctypes.c_int
+        L.lso_render.restype = ctypes.c_int
+        L.lso_render_bwd.restype = ctypes.c_int
+        L.lso_project_bwd.restype = ctypes.c_int
+        L.lso_dupsort_f32.restype = ctypes.c_longlong
+        L.lso_kernel_f.restype = ctypes.c_double
+        L.lso_kernel_f.argtypes = [ctypes.c_int, ctypes.c_double]
+        L.lso_kernel_support.restype = ctypes.c_double
+        L.lso_kernel_support.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.lso_rect.restype = ctypes.c_int
+        L.lso_rect.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_int)]
+        del dp
+        _lib = L
+    return _lib
+
+
+def set_threads(n):
+    lib().lso_set_threads(int(n))
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def params_array(params=None):
+    P = dict(DEFAULTS)
+    if params:
+        P.update(params)
+    bg = P["bg"]
+    return np.array([P["lam"], P["kernel"], P["ags"], P["antialias"], P["eps2d"], P["alpha_min"], P["alpha_max"],
+                     P["t_min"], P["tile_w"], P["tile_h"], bg[0], bg[1], bg[2], P["near"], P["far"],
+                     P["sh_degree"]], dtype=np.float64)
+
+
+def cam_array(cam):
+    vm = np.asarray(cam["viewmat"], dtype=np.float64).reshape(16)
+    return np.concatenate([vm, [cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["width"], cam["height"]]]).astype(
+        np.float64)
+
+
+def project(scene, cam, params=None):
+    """Projected records [n, NP] (FP64) and visibility [n] of a scene."""
+    P = dict(params or {})
+    P.setdefault("sh_degree", scene.sh_degree)
+    n = scene.n
+    out = np.zeros((n, NP))
+    vis = np.zeros(n, dtype=np.uint8)
+    lib().lso_project(ctypes.c_int(n), _p(_d(scene.means)), _p(_d(scene.scales)), _p(_d(scene.quats)),
+                      _p(_d(scene.opac)), _p(_d(scene.sh)), _p(cam_array(cam)), _p(params_array(P)), _p(out),
+                      _p(vis))
+    return out, vis.astype(bool)
+
+
+def render(proj, vis, width, height, params=None, rule_f32=False, dkey=None, brute=False):
+    """Front-to-back composite (Eq. 6) of projected records."""
+    n = proj.shape[0]
+    proj = _d(proj)
+    vis8 = np.ascontiguousarray(vis, dtype=np.uint8)
+    img = np.zeros((height, width, 3))
+    T = np.zeros((height, width))
+    n_last = np.zeros((height, width), dtype=np.int32)
+    last_id = np.zeros((height, width), dtype=np.int32)
+    flags = np.zeros((height, width), dtype=np.uint8)
+    stats = np.zeros(2, dtype=np.int64)
+    dk = None if dkey is None else np.ascontiguousarray(dkey, dtype=np.uint32)
+    lib().lso_render(ctypes.c_int(n), _p(proj), _p(vis8), ctypes.c_int(width), ctypes.c_int(height),
+                     _p(params_array(params)), ctypes.c_int(int(rule_f32)),
+                     _p(dk) if dk is not None else ctypes.c_void_p(0), ctypes.c_int(int(brute)), _p(img), _p(T),
+                     _p(n_last), _p(last_id), _p(flags), _p(stats))
+    return dict(image=img, T=T, n_last=n_last, last_id=last_id, flags=flags.astype(bool), n_eval=int(stats[0]),
+                n_contrib=int(stats[1]))
+
+
+def render_bwd(proj, vis, width, height, gC, gT, params=None, rule_f32=False, dkey=None):
+    """Adjoint of `render` with respect to (mx, my, a, b, c, o_eff, r, g, b)."""
+    n = proj.shape[0]
+    g2d = np.zeros((n, 9))
+    dk = None if dkey is None else np.ascontiguousarray(dkey, dtype=np.uint32)
+    lib().lso_render_bwd(ctypes.c_int(n), _p(_d(proj)), _p(np.ascontiguousarray(vis, dtype=np.uint8)),
+                         ctypes.c_int(width), ctypes.c_int(height), _p(params_array(params)),
+                         ctypes.c_int(int(rule_f32)), _p(dk) if dk is not None else ctypes.c_void_p(0),
+                         _p(_d(gC)), _p(_d(gT)), _p(g2d))
+    return g2d
+
+
+def project_bwd(scene, cam, g2d, params=None):
+    """Gradients of the 3D parameters from g2d (forward-mode dual numbers)."""
+    P = dict(params or {})
+    P.setdefault("sh_degree", scene.sh_degree)
+    n = scene.n
+    K = (scene.sh_degree + 1) ** 2
+    gm = np.zeros((n, 3))
+    gs = np.zeros((n, 3))
+    gq = np.zeros((n, 4))
+    go = np.zeros(n)
+    gsh = np.zeros((n, K, 3))
+    lib().lso_project_bwd(ctypes.c_int(n), _p(_d(scene.means)), _p(_d(scene.scales)), _p(_d(scene.quats)),
+                          _p(_d(scene.opac)), _p(_d(scene.sh)), _p(cam_array(cam)), _p(params_array(P)),
+                          _p(_d(g2d)), _p(gm), _p(gs), _p(gq), _p(go), _p(gsh))
+    return dict(means=gm, scales=gs, quats=gq, opac=go, sh=gsh)
+
+
+def render_scene(scene, cam, params=None, brute=False):
+    P = dict(params or {})
+    P.setdefault("sh_degree", scene.sh_degree)
+    proj, vis = project(scene, cam, P)
+    out = render(proj, vis, cam["width"], cam["height"], P, brute=brute)
+    out["proj"] = proj
+    out["vis"] = vis
+    return out
+
+
+def scene_grads(scene, cam, gC, gT, params=None):
+    """Full adjoint: d/d(3D parameters) of <gC, C> + <gT, T>."""
+    P = dict(params or {})
+    P.setdefault("sh_degree", scene.sh_degree)
+    proj, vis = project(scene, cam, P)
+    g2d = render_bwd(proj, vis, cam["width"], cam["height"], gC, gT, P)
+    g = project_bwd(scene, cam, g2d, P)
+    g["g2d"] = g2d
+    return g
+
+
+def dupsort_f32(foot, dkey, width, height, tile_w, tile_h, cap=None):
+    """Duplicate + stable sort of binary32 footprints: (keys, vals, ranges)."""
+    R = foot.shape[0]
+    foot = np.ascontiguousarray(foot, dtype=np.float32)
+    dkey = np.ascontiguousarray(dkey, dtype=np.uint32)
+    tiles = ((width + tile_w - 1) // tile_w) * ((height + tile_h - 1) // tile_h)
+    ranges = np.zeros(2 * tiles, dtype=np.int32)
+    # upper bound on K: every record covering every tile
+    if cap is None:
+        cap = min(int(R) * tiles, 50_000_000)
+    keys = np.zeros(cap, dtype=np.uint32)
+    vals = np.zeros(cap, dtype=np.uint32)
+    K = lib().lso_dupsort_f32(ctypes.c_longlong(R), _p(foot), _p(dkey), ctypes.c_int(width), ctypes.c_int(height),
+                              ctypes.c_int(tile_w), ctypes.c_int(tile_h), ctypes.c_longlong(cap), _p(keys), _p(vals),
+                              _p(ranges))
+    if K < 0:
+        raise RuntimeError("oracle dupsort capacity exceeded")
+    return keys[:K].copy(), vals[:K].copy(), ranges.reshape(-1, 2)
+
+
+def rect(mx, my, ex, ey, width, height, f32):
+    out = (ctypes.c_int * 4)()
+    ok = lib().lso_rect(mx, my, ex, ey, width, height, int(f32), out)
+    return (list(out) if ok else None)
+
+
+def sh_basis(dirs, deg=3):
+    dirs = _d(dirs)
+    m = dirs.shape[0]
+    out = np.zeros((m, 16))
+    lib().lso_sh_basis(ctypes.c_int(m), ctypes.c_int(deg), _p(dirs), _p(out))
+    return out
+
+
+def kernel_f(k, x):
+    return lib().lso_kernel_f(int(k), float(x))
+
+
+def kernel_support(k, o, amin):
+    return lib().lso_kernel_support(int(k), float(o), float(amin))
+
+
+def records_to_proj(rec):
+    """Random binary32 records (scenes.random_records) in the FP64 NP layout."""
+    n = rec["opac"].shape[0]
+    p = np.zeros((n, NP))
+    p[:, P_MX] = rec["mean2d"][:, 0]
+    p[:, P_MY] = rec["mean2d"][:, 1]
+    p[:, P_A] = rec["conic"][:, 0]
+    p[:, P_B] = rec["conic"][:, 1]
+    p[:, P_C] = rec["conic"][:, 2]
+    p[:, P_O] = rec["opac"]
+    p[:, P_RHO2] = rec["rho2"]
+    p[:, P_DEPTH] = rec["depth"]
+    p[:, P_R:P_BL + 1] = rec["rgb"]
+    p[:, P_EX] = rec["ext"][:, 0]
+    p[:, P_EY] = rec["ext"][:, 1]
+    return p
+
+
+def depth_keys(rec):
+    """Sort bits of random records: binary32 depth bits, 0xFFFFFFFF if hidden."""
+    d = np.ascontiguousarray(rec["depth"], dtype=np.float32).view(np.uint32).copy()
+    d[~rec["visible"]] = 0xFFFFFFFF
+    return d
