@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the linear-splatting rasterizer hot path on GB300.
+
+One step = the whole differentiable frame: projection (a1), duplication and
+radix sort (a2, a3), forward blending (a4), blending adjoint (a5) and
+projection adjoint (a6) of a 3M-primitive SH-degree-3 scene at 1920x1080,
+inputs resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank renders its own replica of the frame (replicas:
+the frame has no exchange step), timing is the max over ranks and `value`
+is the total frames/s of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "diff_3m_1080p"
+METRIC = "1080p fwd+bwd iters/s at 3M prims (fwd frames/s alongside)"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+LANES_PER_SM = 128
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture
+# (profiles/), valid only while the kernel source is the one measured.
+NCU_TRAFFIC = {}
+
+
+def _src_hash(name):
+    p = os.path.join(ROOT, "paper_2411_12440_gb300", "csrc", name)
+    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                for line in out.stdout.strip().splitlines():
+                    self.rows.append([x.strip() for x in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline leg and the reference arm)
+# --------------------------------------------------------------------------
+def oracle_frame_estimate(scene, cam, P, ncores, win=48, prim_sample=4000, seed=0):
+    """Seconds the FP64 oracle needs for one fwd+bwd frame, from a bounded
+    sample: full projection and full tile lists, blending forward and
+    backward on a win x win pixel window scaled by the pixel fraction, and
+    the projection adjoint on a random primitive sample scaled by count."""
+    import numpy as np
+    import oracle
+    oracle.set_threads(ncores)
+    W, H = cam["width"], cam["height"]
+    t0 = time.perf_counter()
+    proj, vis = oracle.project(scene, cam, P)
+    t_proj = time.perf_counter() - t0
+    x0, y0 = W // 2 - win // 2, H // 2 - win // 2
+    window = (x0, x0 + win, y0, y0 + win)
+    empty = (0, 0, 0, 0)
+    t0 = time.perf_counter()
+    oracle.render(proj, vis, W, H, P, window=empty)
+    t_lists = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.render(proj, vis, W, H, P, window=window)
+    t_fwd_win = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    gC = rng.standard_normal((H, W, 3))
+    gT = rng.standard_normal((H, W))
+    t0 = time.perf_counter()
+    g2d = oracle.render_bwd(proj, vis, W, H, gC, gT, P, window=window)
+    t_bwd_win = time.perf_counter() - t0
+    vis_idx = np.nonzero(vis)[0]
+    pick = rng.choice(vis_idx, size=min(prim_sample, len(vis_idx)), replace=False)
+    sub = scene.subset(pick)
+    g2s = rng.standard_normal((len(pick), 9))
+    t0 = time.perf_counter()
+    oracle.project_bwd(sub, cam, g2s, P)
+    t_pbwd = time.perf_counter() - t0
+    frac = (win * win) / float(W * H)
+    est = (t_proj + t_lists + max(t_fwd_win - t_lists, 0.0) / frac + t_lists + max(t_bwd_win - t_lists, 0.0) / frac
+           + t_pbwd * len(vis_idx) / len(pick))
+    sample = ("full projection and tile lists; blending fwd+bwd on a %dx%d window (%.5f of the pixels) and the "
+              "projection adjoint on %d of %d visible primitives, each scaled to the frame" %
+              (win, win, frac, len(pick), len(vis_idx)))
+    spent = t_proj + t_lists + t_fwd_win + t_bwd_win + t_pbwd
+    return est, sample, spent
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle as it stands on the host cores."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2411_12440_gb300 import scenes
+    oracle.build()
+    ncores = os.cpu_count() or 1
+    scene, cams, extra = scenes.make_workload(WORKLOAD)
+    P = dict(sh_degree=3, antialias=int(extra["antialias"]))
+    ests = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        est, sample, _ = oracle_frame_estimate(scene, cams[0], P, ncores, win=16, prim_sample=500, seed=i)
+        if i >= args.warmup:
+            ests.append(est)
+    sec = statistics.median(ests)
+    value = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "prims": scene.n, "width": cams[0]["width"],
+                       "height": cams[0]["height"], "sh_degree": 3},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": ncores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import numpy as np
+    import torch
+    from paper_2411_12440_gb300 import raster, scenes
+
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene, cams, extra = scenes.make_workload(WORKLOAD)
+    cam = cams[0]
+    P = raster.RenderParams(sh_degree=3, antialias=int(extra["antialias"]))
+    rz = raster.Rasterizer(P, device=dev)
+    sp = raster.Splats.from_scene(scene, device=dev)
+    R = sp.n
+    H, W = cam["height"], cam["width"]
+    w, v = scenes.loss_weights(H, W, seed=7)
+    gimg = torch.from_numpy(w).to(dev)
+    gT = torch.from_numpy(v).to(dev)
+    g2d = torch.empty((R, 12), dtype=torch.float32, device=dev)
+    gout = dict(means=torch.empty_like(sp.means), scales=torch.empty_like(sp.scales),
+                quats=torch.empty_like(sp.quats), opac=torch.empty_like(sp.opac), sh=torch.empty_like(sp.sh))
+
+    stage_names = ["project", "duplicate_sort", "blend_fwd", "blend_bwd", "project_bwd"]
+
+    def step(evs=None, bwd=True, splats=None, grad_image=None, grad_t=None, outg=None):
+        spx = splats or sp
+        rec = (lambda i: evs[i].record()) if evs is not None else (lambda i: None)
+        rec(0)
+        proj, _ = rz.project(spx, [cam], counts=False)
+        rec(1)
+        keys, vals, n_keys, ranges = rz.duplicate_sort(proj, R, [cam])
+        rec(2)
+        image, T, n_last = rz.render_fwd(proj, R, cam, ranges, vals)
+        rec(3)
+        if not bwd:
+            return image, T, None
+        g2d.zero_()
+        rz.blend_bwd(proj, R, cam, ranges, vals, T, n_last, grad_image if grad_image is not None else gimg,
+                     grad_t if grad_t is not None else gT, g2d)
+        rec(4)
+        g = rz.project_bwd(spx, [cam], proj, g2d, out=outg or gout)
+        rec(5)
+        return image, T, g
+
+    # capacity from an exact count, then no host syncs inside steps
+    proj, tc = rz.project(sp, [cam], counts=True)
+    K = rz.ensure_capacity(tc)
+    dk = proj.view(torch.uint8)[64 * R:68 * R].view(torch.int32)
+    n_vis = int((dk != -1).sum().item())
+    keys, vals, n_keys, ranges = rz.duplicate_sort(proj, R, [cam])
+    _, _, _, n_eval, n_contrib = rz.render_stats(proj, R, cam, ranges, vals)
+    del proj, tc
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    rz.check_status("warmup")
+
+    # ---------------------------------------------------------------- timed fwd+bwd
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_start.record()
+        for i in range(args.steps):
+            step(evs[i])
+        t_end.record()
+        torch.cuda.synchronize()
+    barrier(ws)
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), ws)
+    rz.check_status("timed steps")
+    stage_ms = {nm: statistics.mean(e[j].elapsed_time(e[j + 1]) for e in evs) for j, nm in enumerate(stage_names)}
+
+    # ---------------------------------------------------------------- timed fwd only
+    barrier(ws)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for i in range(args.steps):
+        step(bwd=False)
+    f1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    fwd_ms = max_over_ranks(f0.elapsed_time(f1), ws) / args.steps
+    rz.check_status("timed forward")
+
+    # ---------------------------------------------------------------- e2e through host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_in = [t.cpu().pin_memory() for t in sp.tensors()] + [gimg.cpu().pin_memory(), gT.cpu().pin_memory()]
+        dev_in = [torch.empty_like(t) for t in sp.tensors()] + [torch.empty_like(gimg), torch.empty_like(gT)]
+        outs = [torch.empty((H, W, 3), dtype=torch.float32).pin_memory()] + \
+            [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in sp.tensors()]
+        h2d = sum(t.numel() * t.element_size() for t in host_in)
+        d2h = sum(t.numel() * t.element_size() for t in outs)
+        spd = raster.Splats(*dev_in[:5], sp.sh_degree)
+        ge = dict(means=torch.empty_like(sp.means), scales=torch.empty_like(sp.scales),
+                  quats=torch.empty_like(sp.quats), opac=torch.empty_like(sp.opac), sh=torch.empty_like(sp.sh))
+
+        def e2e_step():
+            for d, h in zip(dev_in, host_in):
+                d.copy_(h, non_blocking=True)
+            image, T, g = step(splats=spd, grad_image=dev_in[5], grad_t=dev_in[6], outg=ge)
+            outs[0].copy_(image, non_blocking=True)
+            for o, k in zip(outs[1:], ("means", "scales", "quats", "opac", "sh")):
+                o.copy_(g[k], non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        n_e2e = max(3, args.steps // 2)
+        for _ in range(n_e2e):
+            e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier(ws)
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws) / n_e2e
+        rz.check_status("e2e")
+        e2e = {"value": ws * 1e3 / e2e_ms, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    ms = total_ms / args.steps
+    value = ws * 1e3 / ms
+
+    # ---------------------------------------------------------------- roofline of the dominant kernel
+    hbm_peak, peak_src = _peaks()
+    alu_peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12  # Tops/s, FP32 lane instructions
+    kp = 2
+    nt = raster.tiles_of(cam, P)
+    units = {
+        # bytes: mu for all, params + SH3 for visible, 68 B record written (Sec. 3.1 Eq. 1-4)
+        "project": ("hbm", 12 * R + (224 + 68) * n_vis),
+        # depth sort (hist + 4 passes of 16 B), count (order, dkey, foot, rect), emit (rect, order, keys 8 B),
+        # tile sort kp passes of 16 B + its histogram in the emit, ranges
+        "duplicate_sort": ("hbm", 4 * R + 4 * 16 * R + (8 * R + 16 * n_vis + 8 * R) + (12 * R + 8 * K) + kp * 16 * K
+                           + 4 * K + 8 * nt),
+        # FP32 lane operations: 7 per evaluated pair, 11 more per composited pair
+        "blend_fwd": ("alu", 7 * n_eval + 11 * n_contrib),
+        # recompute 7 per evaluated pair + 40 per contributing pair
+        "blend_bwd": ("alu", 7 * n_eval + 40 * n_contrib),
+        # params + SH3 and g2d read, 236 B of gradients written
+        "project_bwd": ("hbm", (236 + 48 + 4 + 236) * R),
+    }
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    bound, amount = units[dom]
+    sec = stage_ms[dom] * 1e-3
+    if bound == "hbm":
+        achieved = amount / sec / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_source": peak_src}
+    else:
+        achieved = amount / sec / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                "frac": achieved / alu_peak, "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz"}
+    tr = NCU_TRAFFIC.get(dom)
+    src = {"blend_fwd": "blend.cu", "blend_bwd": "blend.cu", "project": "project.cu", "project_bwd": "project.cu",
+           "duplicate_sort": "sort.cu"}[dom]
+    roof["kernel"] = dom
+    roof["traffic"] = tr["bytes"] if tr and tr.get("src") == _src_hash(src) else None
+
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "prims": R, "width": W, "height": H, "sh_degree": 3,
+                       "tile": "%dx%d" % (P.tile_w, P.tile_h), "l2": "inputs larger than L2 (708 MB of parameters)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "fwd_fps": ws * 1e3 / fwd_ms, "fwd_ms": fwd_ms,
+            "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "units": {"tile_keys": K, "visible": n_vis, "pairs_evaluated": n_eval, "pairs_composited": n_contrib},
+            "roofline": roof, "clocks": clocks.summary(), "e2e": e2e,
+            # per step: project 1; duplicate_sort 11 + kp (depth hist, scan, 4 passes, count, scan, emit,
+            # scan, kp tile passes, ranges); blend fwd, blend bwd, project bwd 1 each
+            "gpu_launches": args.steps * (1 + (11 + kp) + 3)}
+
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        ncores = os.cpu_count() or 1
+        est, sample, spent = oracle_frame_estimate(scene, cam, dict(sh_degree=3, antialias=int(extra["antialias"])),
+                                                   ncores)
+        line["cpu_baseline"] = {"value": 1.0 / est, "unit": "iters/s", "cores": ncores, "kind": "oracle",
+                                "sample": sample, "seconds_spent": round(spent, 1)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

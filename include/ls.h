@@ -1,0 +1,196 @@
+/*
+ * ls.h -- C ABI of the GB300 (sm_103a) rasterizer for 3D Linear Splatting
+ * (arxiv 2411.12440, "Beyond Gaussians: Fast and High-Fidelity 3D Splatting
+ * with Linear Kernels").
+ *
+ * Every entry point takes plain pointers and sizes.  Unless a parameter says
+ * otherwise:
+ *   - array pointers are DEVICE memory owned by the caller; the library never
+ *     allocates, frees or keeps them after the call returns;
+ *   - structs passed by pointer (ls_params, ls_camera) are HOST memory, read
+ *     during the call only;
+ *   - work is enqueued asynchronously on `stream` (a cudaStream_t, NULL = the
+ *     legacy default stream); the call returns before it runs;
+ *   - the return value reports argument checks and launch errors only:
+ *     LS_ERR_INVALID_ARG before anything is enqueued, LS_ERR_CUDA when a
+ *     launch fails (cudaGetLastError);
+ *   - errors found while the kernels run (key capacity exceeded, a bounded
+ *     device-side wait that gave up) are written to *status_dev, an int32 in
+ *     device memory that the caller zeroes beforehand and reads after
+ *     synchronising; the first error written wins;
+ *   - all floating point is IEEE binary32, row-major.
+ *
+ * Pipeline (one frame): ls_project -> ls_duplicate_sort -> ls_render_fwd,
+ * and for training ls_render_bwd with the forward's T_final / n_last.
+ * ls_render_batch runs the same pipeline for many cameras over one shared
+ * sort and one persistent blending launch.
+ */
+#ifndef LS_H_
+#define LS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LS_OK = 0,
+  LS_ERR_INVALID_ARG = 1,
+  LS_ERR_CUDA = 2,
+  LS_ERR_CAPACITY = 3,   /* more tile keys than key_capacity (device-detected) */
+  LS_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up (device-detected) */
+  LS_ERR_UNSUPPORTED = 5
+} ls_status;
+
+/* Attenuation f(D / lambda) of the Mahalanobis distance D.  Linear is the
+ * paper's kernel (Sec. 3.2 Eq. 9-11 with the alignment of Sec. 3.3.1 Eq. 12);
+ * the others are the family of Appendix B Eq. 21-24. */
+typedef enum {
+  LS_KERNEL_LINEAR = 0,     /* max(0, 1 - x)                 */
+  LS_KERNEL_GAUSSIAN = 1,   /* exp(-x^2 / 2)                 */
+  LS_KERNEL_LAPLACIAN = 2,  /* exp(-x)                       */
+  LS_KERNEL_COSINE = 3,     /* (1 + cos(pi x)) / 2, 0 for x>1 */
+  LS_KERNEL_QUADRATIC = 4   /* max(0, 1 - x^2)               */
+} ls_kernel;
+
+/* Rendering parameters.  Defaults in brackets. */
+typedef struct {
+  float lambda;      /* distribution-alignment factor, Eq. 12 [2.5]; > 0 */
+  int32_t kernel;    /* ls_kernel [LS_KERNEL_LINEAR] */
+  int32_t ags;       /* adaptive gradient scaling, Eq. 13-14: 0 off, 1 w = exp(-D^2),
+                        2 w = exp(-(D/lambda)^2) [0] */
+  int32_t antialias; /* 1: scale opacity by sqrt(det Sigma_2D / det(Sigma_2D + eps2d I))
+                        (Mip-Splatting 2D filter, named in Sec. 4.1) [0] */
+  float eps2d;       /* screen-space dilation added to Sigma_2D [0.3]; >= 0 */
+  float alpha_min;   /* pairs with alpha below this are skipped [1/255]; >= 0 */
+  float alpha_max;   /* alpha clamp [0.999]; in (0, 1) */
+  float t_min;       /* a pixel stops before T would fall below this [1e-4]; >= 0 */
+  int32_t tile_w, tile_h; /* tile shape: 8x8, 16x16 or 32x16 [16x16] */
+  float bg[3];       /* background colour composited behind [0,0,0] */
+  float near_plane, far_plane; /* depth cull (near, far) [0.2, 1e4] */
+  int32_t sh_degree; /* spherical-harmonic degree 0..3 */
+} ls_params;
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  viewmat is the
+ * world-to-camera matrix W of Sec. 3.1 Eq. 3, row-major [R t; 0 0 0 1]. */
+typedef struct {
+  float viewmat[16];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} ls_camera;
+
+#define LS_MAX_CAMS 64
+
+/* Projected-record buffer.  For n primitives seen by n_cams cameras there are
+ * R = n_cams * n records; record r = cam * n + i.  The buffer holds three
+ * consecutive planes, 68 bytes per record (ls_proj_bytes):
+ *   rec  [R][12] float at byte 0:        {mx, my, a, b}, {c, o_eff, rho^2, depth}, {r, g, b, 0}
+ *        screen centre mu' (pixel units, pixel (px,py) covers [px,px+1)x[py,py+1)),
+ *        conic A = (Sigma_2D + eps2d I)^-1 = [[a, b], [b, c]], effective opacity,
+ *        squared support radius in Mahalanobis units, camera depth, colour;
+ *   foot [R][4] float at byte 48*R:      {mx, my, ex, ey} half extents of the support box;
+ *   dkey [R] uint32 at byte 64*R:        binary32 bits of depth, 0xFFFFFFFF when culled.
+ * Fields of culled records other than dkey are unspecified. */
+size_t ls_proj_bytes(int64_t n_records);
+
+/* a1: projection (Sec. 3.1 Eq. 1-4; support of Eq. 12; view-dependent colour).
+ * means [n][3], scales [n][3] (positive, activated), quats [n][4] (w,x,y,z, any
+ * non-zero norm), opacities [n] (activated, in [0,1]), sh [(deg+1)^2][3][n]
+ * (coefficient-major: sh[(k*3+ch)*n + i]); cams: host array of n_cams
+ * (1..LS_MAX_CAMS).  Writes proj (ls_proj_bytes(n_cams*n) bytes) and, when not
+ * NULL, tile_counts [n_cams*n] (tiles each record touches, 0 when culled). */
+ls_status ls_project(int32_t n, const float* means, const float* scales, const float* quats,
+                     const float* opacities, const float* sh, const ls_camera* cams, int32_t n_cams,
+                     const ls_params* params, void* proj, int32_t* tile_counts, int32_t* status_dev,
+                     void* stream);
+
+/* Workspace of ls_duplicate_sort in bytes. */
+size_t ls_duplicate_sort_workspace(int64_t n_records, int64_t key_capacity, int32_t total_tiles);
+
+/* a2+a3: duplication of every visible record into the tiles its support box
+ * touches, and a stable radix sort into front-to-back order per tile
+ * (compositing order of Sec. 3.1 Eq. 6, kept "without alteration", Sec. 3.2).
+ * Tile ids are global over the cameras: camera c's tiles follow those of
+ * cameras 0..c-1, row-major within a camera.  Output, for K keys:
+ *   keys [K] tile ids ascending; vals [K] record ids, ordered inside a tile by
+ *   (depth bits, record id); *n_keys_dev = K (int64, device);
+ *   tile_ranges [total_tiles][2] = [start, end) of each tile in keys/vals.
+ * key_capacity bounds K (<= 2^31-1); when K > key_capacity nothing past the
+ * count is written, ranges are empty and LS_ERR_CAPACITY goes to status_dev.
+ * workspace: device scratch of at least ls_duplicate_sort_workspace bytes,
+ * 256-byte aligned. */
+ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera* cams, int32_t n_cams,
+                            const ls_params* params, int64_t key_capacity, uint32_t* keys, uint32_t* vals,
+                            int64_t* n_keys_dev, int32_t* tile_ranges, void* workspace, size_t ws_bytes,
+                            int32_t* status_dev, void* stream);
+
+/* a4: front-to-back blending of one camera's tiles (Sec. 3.1 Eq. 6 with
+ * alpha = o_eff * f(D/lambda), Eq. 11-12): per pixel centre x', over its
+ * tile's records in order, skip when D^2 > rho^2, alpha = min(alpha_max, .),
+ * skip when alpha < alpha_min, stop before T would drop below t_min.
+ * proj/vals/tile_ranges as produced above for n_cams = 1.  Writes image
+ * [H][W][3] (colour + T * bg), t_final [H][W] and n_last [H][W] (number of
+ * leading entries of the pixel's tile list up to and including the last one
+ * composited: the checkpoint the backward pass resumes from). */
+ls_status ls_render_fwd(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                        const int32_t* tile_ranges, const uint32_t* vals, float* image, float* t_final,
+                        int32_t* n_last, int32_t* status_dev, void* stream);
+
+/* ls_render_fwd that also counts the work units of the tile method into
+ * stats_dev[2] (uint64, device, accumulated: zero it first): [0] evaluated
+ * (pixel, record) pairs -- per tile, its pixels times the entries walked until
+ * the tile's last pixel finished -- and [1] composited pairs (alpha >=
+ * alpha_min, before the stop).  Same outputs as ls_render_fwd; slower (used
+ * to size the roofline of the blending kernels, not on the hot path). */
+ls_status ls_render_stats(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                          const int32_t* tile_ranges, const uint32_t* vals, float* image, float* t_final,
+                          int32_t* n_last, uint64_t* stats_dev, int32_t* status_dev, void* stream);
+
+/* a5: adjoint of ls_render_fwd with respect to each record's (mx, my, a, b,
+ * c, o_eff, r, g, b), recomputing T back to front from t_final / n_last
+ * (Eq. 6); with params->ags the kernel-derivative path is scaled by w(D)
+ * (Eq. 13-14).  grad_image [H][W][3]; grad_t [H][W] or NULL.  g2d [R][12]
+ * float is ACCUMULATED into (zero it first): {gmx, gmy, ga, gb}, {gc, go,
+ * gr, gg}, {gb, 0, 0, 0}. */
+ls_status ls_blend_bwd(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                       const int32_t* tile_ranges, const uint32_t* vals, const float* t_final,
+                       const int32_t* n_last, const float* grad_image, const float* grad_t, float* g2d,
+                       int32_t* status_dev, void* stream);
+
+/* a6: chain rule from g2d [n_cams*n][12] (summed over cameras) to the 3D
+ * parameters of ls_project (Eq. 1-4 and the colour).  Outputs are OVERWRITTEN:
+ * g_means [n][3], g_scales [n][3], g_quats [n][4], g_opac [n],
+ * g_sh [(deg+1)^2][3][n]. */
+ls_status ls_project_bwd(int32_t n, const float* means, const float* scales, const float* quats,
+                         const float* opacities, const float* sh, const ls_camera* cams, int32_t n_cams,
+                         const ls_params* params, const void* proj, const float* g2d, float* g_means,
+                         float* g_scales, float* g_quats, float* g_opac, float* g_sh, int32_t* status_dev,
+                         void* stream);
+
+/* Workspace of ls_render_bwd in bytes (the g2d buffer). */
+size_t ls_render_bwd_workspace(int64_t n_records);
+
+/* a5+a6 in one call for one camera: zeroes a g2d buffer in `workspace`, runs
+ * ls_blend_bwd then ls_project_bwd.  When g2d_out is not NULL the 2D
+ * gradients are also copied there ([n][12] float). */
+ls_status ls_render_bwd(int32_t n, const float* means, const float* scales, const float* quats,
+                        const float* opacities, const float* sh, const ls_camera* cam, const ls_params* params,
+                        const void* proj, const int32_t* tile_ranges, const uint32_t* vals,
+                        const float* t_final, const int32_t* n_last, const float* grad_image,
+                        const float* grad_t, float* g_means, float* g_scales, float* g_quats, float* g_opac,
+                        float* g_sh, float* g2d_out, void* workspace, size_t ws_bytes, int32_t* status_dev,
+                        void* stream);
+
+/* Text of a status code (static storage). */
+const char* ls_status_string(int32_t status);
+
+/* ABI version, bumped on any incompatible change. */
+int32_t ls_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LS_H_ */

@@ -104,8 +104,16 @@ def project(scene, cam, params=None):
     return out, vis.astype(bool)
 
 
-def render(proj, vis, width, height, params=None, rule_f32=False, dkey=None, brute=False):
-    """Front-to-back composite (Eq. 6) of projected records."""
+def _window(window):
+    if window is None:
+        return ctypes.c_void_p(0), None
+    w = np.ascontiguousarray(window, dtype=np.int32)
+    return _p(w), w
+
+
+def render(proj, vis, width, height, params=None, rule_f32=False, dkey=None, brute=False, window=None):
+    """Front-to-back composite (Eq. 6) of projected records; `window` =
+    (x0, x1, y0, y1) restricts it to those pixels (others stay zero)."""
     n = proj.shape[0]
     proj = _d(proj)
     vis8 = np.ascontiguousarray(vis, dtype=np.uint8)
@@ -116,23 +124,26 @@ def render(proj, vis, width, height, params=None, rule_f32=False, dkey=None, bru
     flags = np.zeros((height, width), dtype=np.uint8)
     stats = np.zeros(2, dtype=np.int64)
     dk = None if dkey is None else np.ascontiguousarray(dkey, dtype=np.uint32)
+    wp, _keep = _window(window)
     lib().lso_render(ctypes.c_int(n), _p(proj), _p(vis8), ctypes.c_int(width), ctypes.c_int(height),
                      _p(params_array(params)), ctypes.c_int(int(rule_f32)),
                      _p(dk) if dk is not None else ctypes.c_void_p(0), ctypes.c_int(int(brute)), _p(img), _p(T),
-                     _p(n_last), _p(last_id), _p(flags), _p(stats))
+                     _p(n_last), _p(last_id), _p(flags), _p(stats), wp)
     return dict(image=img, T=T, n_last=n_last, last_id=last_id, flags=flags.astype(bool), n_eval=int(stats[0]),
                 n_contrib=int(stats[1]))
 
 
-def render_bwd(proj, vis, width, height, gC, gT, params=None, rule_f32=False, dkey=None):
-    """Adjoint of `render` with respect to (mx, my, a, b, c, o_eff, r, g, b)."""
+def render_bwd(proj, vis, width, height, gC, gT, params=None, rule_f32=False, dkey=None, window=None):
+    """Adjoint of `render` with respect to (mx, my, a, b, c, o_eff, r, g, b);
+    with `window` only those pixels' terms are summed."""
     n = proj.shape[0]
     g2d = np.zeros((n, 9))
     dk = None if dkey is None else np.ascontiguousarray(dkey, dtype=np.uint32)
+    wp, _keep = _window(window)
     lib().lso_render_bwd(ctypes.c_int(n), _p(_d(proj)), _p(np.ascontiguousarray(vis, dtype=np.uint8)),
                          ctypes.c_int(width), ctypes.c_int(height), _p(params_array(params)),
                          ctypes.c_int(int(rule_f32)), _p(dk) if dk is not None else ctypes.c_void_p(0),
-                         _p(_d(gC)), _p(_d(gT)), _p(g2d))
+                         _p(_d(gC)), _p(_d(gT)), _p(g2d), wp)
     return g2d
 
 
@@ -153,22 +164,23 @@ def project_bwd(scene, cam, g2d, params=None):
     return dict(means=gm, scales=gs, quats=gq, opac=go, sh=gsh)
 
 
-def render_scene(scene, cam, params=None, brute=False):
+def render_scene(scene, cam, params=None, brute=False, window=None):
     P = dict(params or {})
     P.setdefault("sh_degree", scene.sh_degree)
     proj, vis = project(scene, cam, P)
-    out = render(proj, vis, cam["width"], cam["height"], P, brute=brute)
+    out = render(proj, vis, cam["width"], cam["height"], P, brute=brute, window=window)
     out["proj"] = proj
     out["vis"] = vis
     return out
 
 
-def scene_grads(scene, cam, gC, gT, params=None):
-    """Full adjoint: d/d(3D parameters) of <gC, C> + <gT, T>."""
+def scene_grads(scene, cam, gC, gT, params=None, window=None):
+    """Full adjoint: d/d(3D parameters) of <gC, C> + <gT, T> (pixels of
+    `window` only, when given)."""
     P = dict(params or {})
     P.setdefault("sh_degree", scene.sh_degree)
     proj, vis = project(scene, cam, P)
-    g2d = render_bwd(proj, vis, cam["width"], cam["height"], gC, gT, P)
+    g2d = render_bwd(proj, vis, cam["width"], cam["height"], gC, gT, P, window=window)
     g = project_bwd(scene, cam, g2d, P)
     g["g2d"] = g2d
     return g

@@ -544,11 +544,15 @@ long long lso_dupsort_f32(long long R, const float* foot, const uint32_t* dkey, 
 // rule_f32 / dkey select the binary32 tile rule and sort bits (dkey may be
 // NULL: binary32 rounding of the FP64 depth).  Outputs: image [H][W][3] (with
 // background), T [H][W], n_last (tile-list count), last_id, flags, stats[0] =
-// evaluated pairs, stats[1] = composited pairs.
+// evaluated pairs, stats[1] = composited pairs.  window (NULL = whole image):
+// {x0, x1, y0, y1}, only pixels in [x0, x1) x [y0, y1) are composited.
 int lso_render(int n, const double* proj, const unsigned char* vis, int W, int H, const double* parv,
                int rule_f32, const uint32_t* dkey, int brute, double* image, double* T, int32_t* n_last,
-               int32_t* last_id, unsigned char* flags, long long* stats) {
+               int32_t* last_id, unsigned char* flags, long long* stats, const int32_t* window) {
   Par P = unpack_par(parv);
+  // pixel window [x0, x1) x [y0, y1); pixels outside it are left untouched
+  int wx0 = window ? window[0] : 0, wx1 = window ? window[1] : W;
+  int wy0 = window ? window[2] : 0, wy1 = window ? window[3] : H;
   long long n_eval = 0, n_contrib = 0;
   if (brute) {
     std::vector<int> all;
@@ -557,8 +561,8 @@ int lso_render(int n, const double* proj, const unsigned char* vis, int W, int H
     auto key = [&](int i) -> uint32_t { return dkey ? dkey[i] : f32bits(proj[(size_t)i * NP + P_DEPTH]); };
     std::stable_sort(all.begin(), all.end(), [&](int a, int b) { return key(a) < key(b); });
 #pragma omp parallel for num_threads(g_threads) schedule(dynamic, 4) reduction(+ : n_contrib)
-    for (int py = 0; py < H; ++py)
-      for (int px = 0; px < W; ++px) {
+    for (int py = wy0; py < wy1; ++py)
+      for (int px = wx0; px < wx1; ++px) {
         PixOut o = blend_pixel(all, proj, px + 0.5, py + 0.5, P, nullptr);
         size_t pi = (size_t)py * W + px;
         for (int c = 0; c < 3; ++c) image[3 * pi + c] = o.C[c] + o.T * P.bg[c];
@@ -578,8 +582,8 @@ int lso_render(int n, const double* proj, const unsigned char* vis, int W, int H
   for (int t = 0; t < ntiles; ++t) {
     int tx = t % Ls.tiles_x, ty = t / Ls.tiles_x;
     int emax = 0, npix = 0;
-    for (int py = ty * P.tile_h; py < std::min(H, (ty + 1) * P.tile_h); ++py)
-      for (int px = tx * P.tile_w; px < std::min(W, (tx + 1) * P.tile_w); ++px) {
+    for (int py = std::max(ty * P.tile_h, wy0); py < std::min(std::min(H, (ty + 1) * P.tile_h), wy1); ++py)
+      for (int px = std::max(tx * P.tile_w, wx0); px < std::min(std::min(W, (tx + 1) * P.tile_w), wx1); ++px) {
         PixOut o = blend_pixel(Ls.L[t], proj, px + 0.5, py + 0.5, P, nullptr);
         size_t pi = (size_t)py * W + px;
         for (int c = 0; c < 3; ++c) image[3 * pi + c] = o.C[c] + o.T * P.bg[c];
@@ -605,8 +609,11 @@ int lso_render(int n, const double* proj, const unsigned char* vis, int W, int H
 // the kernel-derivative path is scaled by w(D) (Eq. 13-14), so the result is
 // no longer an exact gradient.
 int lso_render_bwd(int n, const double* proj, const unsigned char* vis, int W, int H, const double* parv,
-                   int rule_f32, const uint32_t* dkey, const double* gC, const double* gT, double* g2d) {
+                   int rule_f32, const uint32_t* dkey, const double* gC, const double* gT, double* g2d,
+                   const int32_t* window) {
   Par P = unpack_par(parv);
+  int wx0 = window ? window[0] : 0, wx1 = window ? window[1] : W;
+  int wy0 = window ? window[2] : 0, wy1 = window ? window[3] : H;
   for (size_t i = 0; i < (size_t)n * 9; ++i) g2d[i] = 0.0;
   Lists Ls = build_lists(n, proj, vis, W, H, P, rule_f32, dkey);
   int ntiles = Ls.tiles_x * Ls.tiles_y;
@@ -614,8 +621,8 @@ int lso_render_bwd(int n, const double* proj, const unsigned char* vis, int W, i
   for (int t = 0; t < ntiles; ++t) {
     int tx = t % Ls.tiles_x, ty = t / Ls.tiles_x;
     std::vector<PairRec> rec;
-    for (int py = ty * P.tile_h; py < std::min(H, (ty + 1) * P.tile_h); ++py)
-      for (int px = tx * P.tile_w; px < std::min(W, (tx + 1) * P.tile_w); ++px) {
+    for (int py = std::max(ty * P.tile_h, wy0); py < std::min(std::min(H, (ty + 1) * P.tile_h), wy1); ++py)
+      for (int px = std::max(tx * P.tile_w, wx0); px < std::min(std::min(W, (tx + 1) * P.tile_w), wx1); ++px) {
         rec.clear();
         PixOut o = blend_pixel(Ls.L[t], proj, px + 0.5, py + 0.5, P, &rec);
         size_t pi = (size_t)py * W + px;

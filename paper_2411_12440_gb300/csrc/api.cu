@@ -1,0 +1,349 @@
+// C ABI of libls.so (declared in include/ls.h): argument checks, camera and
+// parameter tables, workspace layout, and the launch sequence of each stage.
+#include <cmath>
+#include <cstring>
+
+#include "kernels.h"
+
+using namespace ls;
+
+namespace {
+
+inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+bool tile_ok(int tw, int th) { return (tw == 8 && th == 8) || (tw == 16 && th == 16) || (tw == 32 && th == 16); }
+
+bool params_ok(const ls_params* p) {
+  if (!p) return false;
+  if (!(p->lambda > 0.f) || p->kernel < 0 || p->kernel > 4 || p->ags < 0 || p->ags > 2) return false;
+  if (!(p->eps2d >= 0.f) || !(p->alpha_min >= 0.f) || !(p->alpha_max > 0.f && p->alpha_max < 1.f)) return false;
+  if (!(p->t_min >= 0.f) || !tile_ok(p->tile_w, p->tile_h)) return false;
+  if (p->sh_degree < 0 || p->sh_degree > 3) return false;
+  if (!(p->near_plane > 0.f && p->far_plane > p->near_plane)) return false;
+  return true;
+}
+
+bool cam_ok(const ls_camera& c) {
+  if (c.width <= 0 || c.height <= 0 || c.width > 16384 || c.height > 16384) return false;
+  if (!(c.fx > 0.f) || !(c.fy > 0.f)) return false;
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(c.viewmat[i])) return false;
+  return true;
+}
+
+ParDev make_par(const ls_params* p) {
+  ParDev P;
+  P.lambda = p->lambda;
+  P.inv_lambda = 1.f / p->lambda;
+  P.kernel = p->kernel;
+  P.ags = p->ags;
+  P.antialias = p->antialias;
+  P.eps2d = p->eps2d;
+  P.alpha_min = p->alpha_min;
+  P.alpha_max = p->alpha_max;
+  P.t_min = p->t_min;
+  P.tile_w = p->tile_w;
+  P.tile_h = p->tile_h;
+  for (int i = 0; i < 3; ++i) P.bg[i] = p->bg[i];
+  P.near_plane = p->near_plane;
+  P.far_plane = p->far_plane;
+  P.sh_degree = p->sh_degree;
+  return P;
+}
+
+// Returns false on a bad camera.  Tile ids are global: camera c's tiles start
+// after those of cameras 0..c-1.
+bool make_cams(const ls_camera* cams, int n_cams, const ls_params* p, CamTable& T, int64_t* total_tiles) {
+  if (!cams || n_cams < 1 || n_cams > LS_MAX_CAMS) return false;
+  std::memset(&T, 0, sizeof(T));
+  T.n = n_cams;
+  int64_t base = 0;
+  for (int c = 0; c < n_cams; ++c) {
+    const ls_camera& s = cams[c];
+    if (!cam_ok(s)) return false;
+    CamDev& d = T.c[c];
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) d.R[3 * i + j] = s.viewmat[4 * i + j];
+      d.t[i] = s.viewmat[4 * i + 3];
+    }
+    for (int j = 0; j < 3; ++j) {
+      double v = 0.0;
+      for (int i = 0; i < 3; ++i) v -= (double)s.viewmat[4 * i + j] * (double)s.viewmat[4 * i + 3];
+      d.campos[j] = (float)v;
+    }
+    d.fx = s.fx;
+    d.fy = s.fy;
+    d.cx = s.cx;
+    d.cy = s.cy;
+    d.W = s.width;
+    d.H = s.height;
+    d.lim_xl = (float)((s.cx + 0.15 * s.width) / s.fx);
+    d.lim_xh = (float)((s.width - s.cx + 0.15 * s.width) / s.fx);
+    d.lim_yl = (float)((s.cy + 0.15 * s.height) / s.fy);
+    d.lim_yh = (float)((s.height - s.cy + 0.15 * s.height) / s.fy);
+    d.tiles_x = (s.width + p->tile_w - 1) / p->tile_w;
+    d.tiles_y = (s.height + p->tile_h - 1) / p->tile_h;
+    d.tile_base = (int)base;
+    base += (int64_t)d.tiles_x * d.tiles_y;
+  }
+  if (base > (1 << 24)) return false;
+  if (total_tiles) *total_tiles = base;
+  return true;
+}
+
+int key_passes_for(int64_t total_tiles) {
+  int bits = 1;
+  while ((1ll << bits) < total_tiles) ++bits;
+  return (bits + 7) / 8;
+}
+
+ProjPtr proj_planes(void* proj, int64_t R) {
+  char* b = static_cast<char*>(proj);
+  return ProjPtr{reinterpret_cast<float4*>(b), reinterpret_cast<float4*>(b + 48 * (size_t)R),
+                 reinterpret_cast<uint32_t*>(b + 64 * (size_t)R)};
+}
+ProjCPtr proj_cplanes(const void* proj, int64_t R) {
+  const char* b = static_cast<const char*>(proj);
+  return ProjCPtr{reinterpret_cast<const float4*>(b), reinterpret_cast<const float4*>(b + 48 * (size_t)R),
+                  reinterpret_cast<const uint32_t*>(b + 64 * (size_t)R)};
+}
+
+// Workspace of ls_duplicate_sort, in carve order.
+struct DupWs {
+  uint32_t *dk_a, *dv_a, *dk_b, *dv_b;  // depth sort ping-pong [R]
+  uint2* rect;                          // [R]
+  uint32_t* block_sums;                 // [nb]
+  int64_t* n_valid;
+  uint32_t *k_alt, *v_alt;              // tile sort ping-pong [cap]
+  void* depth_scratch;
+  void* tile_scratch;
+  size_t zero_begin, zero_bytes;        // byte range cleared before every call
+  size_t total;
+};
+
+DupWs dup_layout(char* base, int64_t R, int64_t cap, int key_passes) {
+  DupWs w;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base + off;
+    off += al256(bytes);
+    return p;
+  };
+  const size_t Rz = (size_t)(R > 0 ? R : 1), Cz = (size_t)(cap > 0 ? cap : 1);
+  w.dk_a = reinterpret_cast<uint32_t*>(take(4 * Rz));
+  w.dv_a = reinterpret_cast<uint32_t*>(take(4 * Rz));
+  w.dk_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
+  w.dv_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
+  w.rect = reinterpret_cast<uint2*>(take(8 * Rz));
+  w.block_sums = reinterpret_cast<uint32_t*>(take(4 * ((Rz + DUP_BLOCK - 1) / DUP_BLOCK)));
+  w.n_valid = reinterpret_cast<int64_t*>(take(8));
+  w.k_alt = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.v_alt = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.zero_begin = off;
+  w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4));
+  w.tile_scratch = take(sort_scratch_bytes((int64_t)Cz, key_passes));
+  w.zero_bytes = off - w.zero_begin;
+  w.total = off;
+  return w;
+}
+
+#define LS_TRY(expr)                          \
+  do {                                        \
+    if ((expr) != cudaSuccess) return LS_ERR_CUDA; \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int32_t ls_version(void) { return 1; }
+
+const char* ls_status_string(int32_t s) {
+  switch (s) {
+    case LS_OK: return "ok";
+    case LS_ERR_INVALID_ARG: return "invalid argument";
+    case LS_ERR_CUDA: return "CUDA launch error";
+    case LS_ERR_CAPACITY: return "tile-key capacity exceeded";
+    case LS_ERR_TIMEOUT: return "device-side wait timed out";
+    case LS_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+size_t ls_proj_bytes(int64_t n_records) { return n_records > 0 ? (size_t)n_records * 68 : 0; }
+
+ls_status ls_project(int32_t n, const float* means, const float* scales, const float* quats,
+                     const float* opacities, const float* sh, const ls_camera* cams, int32_t n_cams,
+                     const ls_params* params, void* proj, int32_t* tile_counts, int32_t* status_dev,
+                     void* stream) {
+  if (n < 0 || !params_ok(params)) return LS_ERR_INVALID_ARG;
+  CamTable T;
+  if (!make_cams(cams, n_cams, params, T, nullptr)) return LS_ERR_INVALID_ARG;
+  if ((int64_t)n * n_cams > 0x7FFFFFFFll) return LS_ERR_INVALID_ARG;
+  if (n == 0) return LS_OK;
+  if (!means || !scales || !quats || !opacities || !sh || !proj) return LS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(quats) % 16 || reinterpret_cast<uintptr_t>(proj) % 16) return LS_ERR_INVALID_ARG;
+  ParDev P = make_par(params);
+  LS_TRY(launch_project_fwd(n, means, scales, quats, opacities, sh, T, P, proj_planes(proj, (int64_t)n * n_cams),
+                            tile_counts, static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+size_t ls_duplicate_sort_workspace(int64_t n_records, int64_t key_capacity, int32_t total_tiles) {
+  if (n_records < 0 || key_capacity < 0 || total_tiles < 1) return 0;
+  return dup_layout(nullptr, n_records, key_capacity, key_passes_for(total_tiles)).total;
+}
+
+ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera* cams, int32_t n_cams,
+                            const ls_params* params, int64_t key_capacity, uint32_t* keys, uint32_t* vals,
+                            int64_t* n_keys_dev, int32_t* tile_ranges, void* workspace, size_t ws_bytes,
+                            int32_t* status_dev, void* stream) {
+  if (n_records < 0 || !params_ok(params)) return LS_ERR_INVALID_ARG;
+  if (key_capacity < 0 || key_capacity > 0x7FFFFFFFll || n_records > 0xFFFFFFFFll) return LS_ERR_INVALID_ARG;
+  CamTable T;
+  int64_t total_tiles = 0;
+  if (!make_cams(cams, n_cams, params, T, &total_tiles)) return LS_ERR_INVALID_ARG;
+  if (n_records % n_cams) return LS_ERR_INVALID_ARG;
+  if (!n_keys_dev || !tile_ranges || !workspace) return LS_ERR_INVALID_ARG;
+  if (key_capacity > 0 && (!keys || !vals)) return LS_ERR_INVALID_ARG;
+  if (n_records > 0 && !proj) return LS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return LS_ERR_INVALID_ARG;
+  const int kp = key_passes_for(total_tiles);
+  DupWs w = dup_layout(static_cast<char*>(workspace), n_records, key_capacity, kp);
+  if (ws_bytes < w.total) return LS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ParDev P = make_par(params);
+  const int64_t R = n_records;
+  const int n_per_cam = (int)(R / n_cams);
+  ProjCPtr pp = proj_cplanes(proj, R);
+
+  LS_TRY(cudaMemsetAsync(static_cast<char*>(workspace) + w.zero_begin, 0, w.zero_bytes, st));
+  // depth sort of the records: key = binary32 depth bits (0xFFFFFFFF when
+  // culled), value = record id; four 8-bit passes, the last lands in (dk_a, dv_a)
+  SortScratch ds = sort_scratch_carve(w.depth_scratch, R > 0 ? R : 1, 4);
+  if (R > 0) {
+    LS_TRY(launch_radix_hist(pp.dkey, nullptr, R, 0, 4, ds.hist, st));
+    LS_TRY(launch_radix_scan(ds.hist, 4, st));
+    LS_TRY(launch_onesweep_pass(pp.dkey, nullptr, w.dk_b, w.dv_b, nullptr, R, R, 0, 0, ds, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 1, ds, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_a, w.dv_a, w.dk_b, w.dv_b, nullptr, R, R, 0, 2, ds, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 3, ds, status_dev, st));
+    LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n_per_cam, P, w.rect, w.block_sums, st));
+  }
+  LS_TRY(launch_dup_scan(R, w.block_sums, key_capacity, n_keys_dev, w.n_valid, status_dev, st));
+  // emission goes to the buffer that makes the last tile-sort pass end in
+  // the caller's keys/vals
+  uint32_t* ek = (kp % 2 == 0) ? keys : w.k_alt;
+  uint32_t* ev = (kp % 2 == 0) ? vals : w.v_alt;
+  uint32_t* ok = (kp % 2 == 0) ? w.k_alt : keys;
+  uint32_t* ov = (kp % 2 == 0) ? w.v_alt : vals;
+  SortScratch ts = sort_scratch_carve(w.tile_scratch, key_capacity > 0 ? key_capacity : 1, kp);
+  if (R > 0 && key_capacity > 0) {
+    LS_TRY(launch_dup_emit(R, w.dv_a, w.rect, w.block_sums, T, n_per_cam, w.n_valid, ek, ev, kp, ts.hist, st));
+    LS_TRY(launch_radix_scan(ts.hist, kp, st));
+    for (int p = 0; p < kp; ++p) {
+      LS_TRY(launch_onesweep_pass(ek, ev, ok, ov, w.n_valid, 0, key_capacity, 0, p, ts, status_dev, st));
+      std::swap(ek, ok);
+      std::swap(ev, ov);
+    }
+  }
+  LS_TRY(launch_tile_ranges(keys, w.n_valid, key_capacity, tile_ranges, (int)total_tiles, st));
+  return LS_OK;
+}
+
+ls_status ls_render_fwd(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                        const int32_t* tile_ranges, const uint32_t* vals, float* image, float* t_final,
+                        int32_t* n_last, int32_t* status_dev, void* stream) {
+  if (!params_ok(params) || n_records < 0) return LS_ERR_INVALID_ARG;
+  CamTable T;
+  if (!make_cams(cam, 1, params, T, nullptr)) return LS_ERR_INVALID_ARG;
+  if (!tile_ranges || !image || !t_final || !n_last) return LS_ERR_INVALID_ARG;
+  if (n_records > 0 && (!proj || !vals)) return LS_ERR_INVALID_ARG;
+  (void)status_dev;
+  ProjCPtr pp = proj_cplanes(proj, n_records);
+  LS_TRY(launch_blend_fwd(pp.rec, T.c[0], make_par(params), reinterpret_cast<const int2*>(tile_ranges), vals, image,
+                          t_final, n_last, nullptr, static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+ls_status ls_render_stats(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                          const int32_t* tile_ranges, const uint32_t* vals, float* image, float* t_final,
+                          int32_t* n_last, uint64_t* stats_dev, int32_t* status_dev, void* stream) {
+  if (!params_ok(params) || n_records < 0) return LS_ERR_INVALID_ARG;
+  CamTable T;
+  if (!make_cams(cam, 1, params, T, nullptr)) return LS_ERR_INVALID_ARG;
+  if (!tile_ranges || !image || !t_final || !n_last || !stats_dev) return LS_ERR_INVALID_ARG;
+  if (n_records > 0 && (!proj || !vals)) return LS_ERR_INVALID_ARG;
+  (void)status_dev;
+  ProjCPtr pp = proj_cplanes(proj, n_records);
+  LS_TRY(launch_blend_fwd(pp.rec, T.c[0], make_par(params), reinterpret_cast<const int2*>(tile_ranges), vals, image,
+                          t_final, n_last, reinterpret_cast<unsigned long long*>(stats_dev),
+                          static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+ls_status ls_blend_bwd(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                       const int32_t* tile_ranges, const uint32_t* vals, const float* t_final,
+                       const int32_t* n_last, const float* grad_image, const float* grad_t, float* g2d,
+                       int32_t* status_dev, void* stream) {
+  if (!params_ok(params) || n_records < 0) return LS_ERR_INVALID_ARG;
+  CamTable T;
+  if (!make_cams(cam, 1, params, T, nullptr)) return LS_ERR_INVALID_ARG;
+  if (!tile_ranges || !t_final || !n_last || !grad_image) return LS_ERR_INVALID_ARG;
+  if (n_records > 0 && (!proj || !vals || !g2d)) return LS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(g2d) % 16) return LS_ERR_INVALID_ARG;
+  (void)status_dev;
+  ProjCPtr pp = proj_cplanes(proj, n_records);
+  LS_TRY(launch_blend_bwd(pp.rec, T.c[0], make_par(params), reinterpret_cast<const int2*>(tile_ranges), vals,
+                          t_final, n_last, grad_image, grad_t, g2d, static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+ls_status ls_project_bwd(int32_t n, const float* means, const float* scales, const float* quats,
+                         const float* opacities, const float* sh, const ls_camera* cams, int32_t n_cams,
+                         const ls_params* params, const void* proj, const float* g2d, float* g_means,
+                         float* g_scales, float* g_quats, float* g_opac, float* g_sh, int32_t* status_dev,
+                         void* stream) {
+  if (n < 0 || !params_ok(params)) return LS_ERR_INVALID_ARG;
+  CamTable T;
+  if (!make_cams(cams, n_cams, params, T, nullptr)) return LS_ERR_INVALID_ARG;
+  if (n == 0) return LS_OK;
+  if (!means || !scales || !quats || !opacities || !sh || !proj || !g2d || !g_means || !g_scales || !g_quats ||
+      !g_opac || !g_sh)
+    return LS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(quats) % 16 || reinterpret_cast<uintptr_t>(g_quats) % 16 ||
+      reinterpret_cast<uintptr_t>(g2d) % 16)
+    return LS_ERR_INVALID_ARG;
+  (void)status_dev;
+  LS_TRY(launch_project_bwd(n, means, scales, quats, opacities, sh, T, make_par(params),
+                            proj_cplanes(proj, (int64_t)n * n_cams), g2d, g_means, g_scales, g_quats, g_opac, g_sh,
+                            static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+size_t ls_render_bwd_workspace(int64_t n_records) { return n_records > 0 ? al256((size_t)n_records * 48) : 256; }
+
+ls_status ls_render_bwd(int32_t n, const float* means, const float* scales, const float* quats,
+                        const float* opacities, const float* sh, const ls_camera* cam, const ls_params* params,
+                        const void* proj, const int32_t* tile_ranges, const uint32_t* vals,
+                        const float* t_final, const int32_t* n_last, const float* grad_image,
+                        const float* grad_t, float* g_means, float* g_scales, float* g_quats, float* g_opac,
+                        float* g_sh, float* g2d_out, void* workspace, size_t ws_bytes, int32_t* status_dev,
+                        void* stream) {
+  if (n < 0 || !params_ok(params)) return LS_ERR_INVALID_ARG;
+  if (!workspace || ws_bytes < ls_render_bwd_workspace(n)) return LS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return LS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* g2d = static_cast<float*>(workspace);
+  if (n > 0) LS_TRY(cudaMemsetAsync(g2d, 0, (size_t)n * 48, st));
+  ls_status s = ls_blend_bwd(proj, n, cam, params, tile_ranges, vals, t_final, n_last, grad_image, grad_t, g2d,
+                             status_dev, stream);
+  if (s != LS_OK) return s;
+  s = ls_project_bwd(n, means, scales, quats, opacities, sh, cam, 1, params, proj, g2d, g_means, g_scales, g_quats,
+                     g_opac, g_sh, status_dev, stream);
+  if (s != LS_OK) return s;
+  if (g2d_out && n > 0) LS_TRY(cudaMemcpyAsync(g2d_out, g2d, (size_t)n * 48, cudaMemcpyDeviceToDevice, st));
+  return LS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Host-side launchers of the sm_103a kernels (internal to libls.so).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace ls {
+
+// ---- projection (project.cu)
+cudaError_t launch_project_fwd(int n, const float* means, const float* scales, const float* quats,
+                               const float* opac, const float* sh, const CamTable& cams, const ParDev& P,
+                               ProjPtr out, int32_t* tile_counts, cudaStream_t st);
+cudaError_t launch_project_bwd(int n, const float* means, const float* scales, const float* quats,
+                               const float* opac, const float* sh, const CamTable& cams, const ParDev& P,
+                               ProjCPtr proj, const float* g2d, float* g_means, float* g_scales, float* g_quats,
+                               float* g_opac, float* g_sh, cudaStream_t st);
+
+// ---- onesweep radix sort (sort.cu)
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 15;
+constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per partition
+constexpr int RADIX = 256;
+
+// Scratch of one sort of up to `cap` keys over `passes` 8-bit digits.
+struct SortScratch {
+  uint32_t* hist;      // [passes][RADIX] digit counts, scanned in place
+  uint32_t* part_ctr;  // [passes] partition tickets
+  uint64_t* lookback;  // [passes][parts][RADIX]
+  int64_t parts;
+};
+size_t sort_scratch_bytes(int64_t cap, int passes);
+SortScratch sort_scratch_carve(void* base, int64_t cap, int passes);
+
+// Digit histograms of all passes in one read (skipped when the caller has
+// filled `hist` itself); then the exclusive scans.
+cudaError_t launch_radix_hist(const uint32_t* keys, const int64_t* n_dev, int64_t n_host, int begin_bit,
+                              int passes, uint32_t* hist, cudaStream_t st);
+cudaError_t launch_radix_scan(uint32_t* hist, int passes, cudaStream_t st);
+// One onesweep pass (digit `pass`, bits [begin_bit + 8 pass, +8)).
+// vals_in == nullptr means the identity values 0..n-1.  n is read from
+// n_dev when not null, else n_host; the grid covers `cap` keys.
+cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                 uint32_t* vals_out, const int64_t* n_dev, int64_t n_host, int64_t cap,
+                                 int begin_bit, int pass, const SortScratch& s, int32_t* status,
+                                 cudaStream_t st);
+
+// ---- duplication and tile ranges (duplicate.cu)
+constexpr int DUP_THREADS = 256;
+constexpr int DUP_ITEMS = 4;
+constexpr int DUP_BLOCK = DUP_THREADS * DUP_ITEMS;
+cudaError_t launch_dup_count(int64_t R, const uint32_t* order, const uint32_t* dkey_sorted, const float4* foot,
+                             const CamTable& cams, int n_per_cam, const ParDev& P, uint2* rect_sorted,
+                             uint32_t* block_sums, cudaStream_t st);
+cudaError_t launch_dup_scan(int64_t R, uint32_t* block_sums, int64_t cap, int64_t* n_keys_dev, int64_t* n_valid_dev,
+                            int32_t* status, cudaStream_t st);
+cudaError_t launch_dup_emit(int64_t R, const uint32_t* order, const uint2* rect_sorted, const uint32_t* block_offs,
+                            const CamTable& cams, int n_per_cam, const int64_t* n_valid_dev, uint32_t* keys,
+                            uint32_t* vals, int key_passes, uint32_t* tile_hist, cudaStream_t st);
+cudaError_t launch_tile_ranges(const uint32_t* keys, const int64_t* n_valid_dev, int64_t cap, int32_t* ranges,
+                               int total_tiles, cudaStream_t st);
+
+// ---- blending (blend.cu)
+cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
+                             const uint32_t* vals, float* image, float* t_final, int32_t* n_last,
+                             unsigned long long* stats, cudaStream_t st);
+cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
+                             const uint32_t* vals, const float* t_final, const int32_t* n_last,
+                             const float* grad_image, const float* grad_t, float* g2d, cudaStream_t st);
+
+}  // namespace ls

@@ -1,0 +1,243 @@
+// a3: onesweep LSD radix sort of (uint32 key, uint32 value) pairs with 8-bit
+// digits (single-pass prefix by decoupled look-back).  Stable, so sorting the
+// duplication output by tile id keeps each tile's entries in the depth order
+// they were emitted in: the front-to-back order of Sec. 3.1 Eq. 6.
+//
+// Per pass every partition of SORT_PART keys is claimed with an atomic ticket
+// (so a partition only ever waits on partitions that are already running),
+// ranked in registers with warp ballots, published as a per-digit aggregate,
+// completed by looking back over its predecessors, staged in shared memory in
+// sorted order and written out in digit runs.  Every wait on a predecessor is
+// bounded: after SPIN_LIMIT polls the kernel records LS_ERR_TIMEOUT and
+// finishes with in-bounds writes only.
+#include "kernels.h"
+
+namespace ls {
+
+namespace {
+
+constexpr uint64_t LB_AGG = 1ull << 62;
+constexpr uint64_t LB_INC = 1ull << 63;
+constexpr uint64_t LB_VAL = (1ull << 62) - 1;
+constexpr int SPIN_LIMIT = 1 << 21;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+static_assert(SORT_THREADS == RADIX, "one thread per digit");
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Inclusive scan of one value per thread over a block of SORT_THREADS.
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) s_warp[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < SORT_WARPS ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < SORT_WARPS; o <<= 1) {
+      uint32_t u = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += u;
+    }
+    if (lane < SORT_WARPS) s_warp[lane] = w;
+  }
+  __syncthreads();
+  return v + (warp > 0 ? s_warp[warp - 1] : 0);
+}
+
+__global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t* __restrict__ keys, const int64_t* n_dev,
+                                                         int64_t n_host, int begin_bit, int passes,
+                                                         uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_h[4][RADIX];
+  for (int i = threadIdx.x; i < 4 * RADIX; i += blockDim.x) (&s_h[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t n = n_dev ? *n_dev : n_host;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t k = keys[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(k >> (begin_bit + 8 * p)) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) {
+    uint32_t v = (&s_h[0][0])[i];
+    if (v) atomicAdd(&hist[i], v);
+  }
+}
+
+__global__ void __launch_bounds__(RADIX) radix_scan_kernel(uint32_t* hist) {
+  __shared__ uint32_t s_warp[SORT_WARPS];
+  uint32_t* h = hist + (size_t)blockIdx.x * RADIX;
+  uint32_t v = h[threadIdx.x];
+  uint32_t incl = block_incl_scan(v, s_warp);
+  h[threadIdx.x] = incl - v;
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) onesweep_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, const int64_t* n_dev, int64_t n_host, int shift,
+    const uint32_t* __restrict__ digit_base, uint64_t* lookback, uint32_t* part_ctr, int32_t* status) {
+  __shared__ uint32_t s_keys[SORT_PART];
+  __shared__ uint32_t s_vals[SORT_PART];
+  __shared__ uint32_t s_whist[SORT_WARPS][RADIX];
+  __shared__ uint32_t s_local[RADIX];
+  __shared__ uint32_t s_glob[RADIX];
+  __shared__ uint32_t s_warp[SORT_WARPS];
+  __shared__ uint32_t s_part;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&s_whist[0][0])[i] = 0;
+  if (tid == 0) s_part = atomicAdd(part_ctr, 1u);
+  __syncthreads();
+  const int64_t n = n_dev ? *n_dev : n_host;
+  const uint32_t part = s_part;
+  const int64_t base = (int64_t)part * SORT_PART;
+  if (base >= n) return;  // block-uniform
+
+  // warp-striped load: warp w holds positions base + w*32*ITEMS + i*32 + lane
+  const int64_t wbase = base + (int64_t)warp * 32 * SORT_ITEMS;
+  uint32_t k[SORT_ITEMS];
+  uint32_t rank[SORT_ITEMS];
+#pragma unroll
+  for (int i = 0; i < SORT_ITEMS; ++i) {
+    int64_t idx = wbase + i * 32 + lane;
+    k[i] = idx < n ? keys_in[idx] : 0xFFFFFFFFu;
+  }
+  // rank inside the warp: peers with the same digit from 8 ballots; items are
+  // visited in position order, so ranks are stable
+  const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < SORT_ITEMS; ++i) {
+    const bool valid = wbase + i * 32 + lane < n;
+    const uint32_t d = (k[i] >> shift) & 255u;
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const uint32_t bit = (d >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
+    const uint32_t before = s_whist[warp][d];
+    __syncwarp();
+    rank[i] = before + __popc(peers & lt);
+    if (valid && lane == 31 - __clz(peers)) s_whist[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // one thread per digit: warp-exclusive offsets, block count, look-back
+  {
+    const int d = tid;
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < SORT_WARPS; ++w) {
+      uint32_t c = s_whist[w][d];
+      s_whist[w][d] = run;
+      run += c;
+    }
+    uint64_t* my = lookback + (size_t)part * RADIX + d;
+    st_relaxed_u64(my, (part == 0 ? LB_INC : LB_AGG) | (uint64_t)run);
+    const uint32_t incl = block_incl_scan(run, s_warp);
+    s_local[d] = incl - run;
+    uint64_t prefix = 0;
+    if (part > 0) {
+      int64_t p = (int64_t)part - 1;
+      int spins = 0;
+      while (p >= 0) {
+        const uint64_t v = ld_relaxed_u64(lookback + (size_t)p * RADIX + d);
+        if ((v & (LB_AGG | LB_INC)) == 0) {
+          if (++spins > SPIN_LIMIT) {
+            set_status(status, LS_ERR_TIMEOUT);
+            break;
+          }
+          continue;
+        }
+        prefix += v & LB_VAL;
+        if (v & LB_INC) break;
+        --p;
+      }
+      st_relaxed_u64(my, LB_INC | (prefix + run));
+    }
+    s_glob[d] = digit_base[d] + (uint32_t)prefix - s_local[d];
+  }
+  __syncthreads();
+
+  // stage in block-sorted order
+#pragma unroll
+  for (int i = 0; i < SORT_ITEMS; ++i) {
+    const int64_t idx = wbase + i * 32 + lane;
+    if (idx < n) {
+      const uint32_t d = (k[i] >> shift) & 255u;
+      const uint32_t pos = s_local[d] + s_whist[warp][d] + rank[i];
+      s_keys[pos] = k[i];
+      s_vals[pos] = vals_in ? vals_in[idx] : (uint32_t)idx;
+    }
+  }
+  __syncthreads();
+  // digit runs go to consecutive global positions
+  const int n_in = (int)(n - base < SORT_PART ? n - base : SORT_PART);
+  for (int s = tid; s < n_in; s += SORT_THREADS) {
+    const uint32_t key = s_keys[s];
+    const uint32_t dst = s_glob[(key >> shift) & 255u] + (uint32_t)s;
+    if (dst < (uint64_t)n) {
+      keys_out[dst] = key;
+      vals_out[dst] = s_vals[s];
+    }
+  }
+}
+
+inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t sort_scratch_bytes(int64_t cap, int passes) {
+  int64_t parts = cap > 0 ? (cap + SORT_PART - 1) / SORT_PART : 1;
+  return al256((size_t)passes * RADIX * 4) + al256((size_t)passes * 4) +
+         al256((size_t)passes * parts * RADIX * 8);
+}
+
+SortScratch sort_scratch_carve(void* base, int64_t cap, int passes) {
+  SortScratch s;
+  s.parts = cap > 0 ? (cap + SORT_PART - 1) / SORT_PART : 1;
+  char* p = static_cast<char*>(base);
+  s.hist = reinterpret_cast<uint32_t*>(p);
+  p += al256((size_t)passes * RADIX * 4);
+  s.part_ctr = reinterpret_cast<uint32_t*>(p);
+  p += al256((size_t)passes * 4);
+  s.lookback = reinterpret_cast<uint64_t*>(p);
+  return s;
+}
+
+cudaError_t launch_radix_hist(const uint32_t* keys, const int64_t* n_dev, int64_t n_host, int begin_bit,
+                              int passes, uint32_t* hist, cudaStream_t st) {
+  int blocks = 152 * 4;
+  radix_hist_kernel<<<blocks, 256, 0, st>>>(keys, n_dev, n_host, begin_bit, passes, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_radix_scan(uint32_t* hist, int passes, cudaStream_t st) {
+  radix_scan_kernel<<<passes, RADIX, 0, st>>>(hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                 uint32_t* vals_out, const int64_t* n_dev, int64_t n_host, int64_t cap,
+                                 int begin_bit, int pass, const SortScratch& s, int32_t* status,
+                                 cudaStream_t st) {
+  unsigned grid = ceil_div(cap > 0 ? cap : 1, SORT_PART);
+  onesweep_kernel<<<grid, SORT_THREADS, 0, st>>>(keys_in, vals_in, keys_out, vals_out, n_dev, n_host,
+                                                 begin_bit + 8 * pass, s.hist + (size_t)pass * RADIX,
+                                                 s.lookback + (size_t)pass * s.parts * RADIX, s.part_ctr + pass,
+                                                 status);
+  return cudaGetLastError();
+}
+
+}  // namespace ls

@@ -1,0 +1,110 @@
+"""Host-side checks that need no GPU: libls.so builds for sm_103a, loads, and
+exports every entry point include/ls.h declares; host argument checks reject
+bad calls before anything is launched; struct layouts match the header."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2411_12440_gb300 import build, _native
+    build.build()
+    return _native.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ls.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(ls_[a-z_0-9]+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_prototypes_cover_header():
+    from paper_2411_12440_gb300 import _native
+    assert set(_declared()) <= set(_native.PROTOTYPES)
+
+
+def test_struct_layouts_match_header(L, tmp_path):
+    """ctypes mirrors have the size and field offsets gcc gives the C structs."""
+    import subprocess
+    from paper_2411_12440_gb300 import _native as N
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "ls.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(ls_params), offsetof(ls_params, bg), offsetof(ls_params, sh_degree),
+         sizeof(ls_camera), offsetof(ls_camera, width));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == [ctypes.sizeof(N.LsParams), N.LsParams.bg.offset, N.LsParams.sh_degree.offset,
+                   ctypes.sizeof(N.LsCamera), N.LsCamera.width.offset]
+
+
+def test_version_and_status_strings(L):
+    assert L.ls_version() == 1
+    assert L.ls_status_string(3) == b"tile-key capacity exceeded"
+    assert L.ls_status_string(99) == b"unknown status"
+    assert L.ls_proj_bytes(10) == 680
+
+
+def test_workspace_queries(L):
+    a = L.ls_duplicate_sort_workspace(1000, 10000, 256)
+    b = L.ls_duplicate_sort_workspace(1000, 20000, 256)
+    assert 0 < a < b
+    assert L.ls_duplicate_sort_workspace(-1, 10, 10) == 0
+    assert L.ls_render_bwd_workspace(1000) >= 48000
+
+
+def test_host_argument_checks_reject_before_launch(L):
+    """Invalid parameters return LS_ERR_INVALID_ARG without touching the GPU
+    (the pointers below are never dereferenced)."""
+    from paper_2411_12440_gb300 import raster
+    from paper_2411_12440_gb300 import scenes
+    cam = raster.cam_struct(scenes.identity_camera(64, 64))
+    bad = [raster.RenderParams(lam=0.0), raster.RenderParams(tile_w=12), raster.RenderParams(sh_degree=4),
+           raster.RenderParams(alpha_max=1.0), raster.RenderParams(kernel=7), raster.RenderParams(near=2, far=1)]
+    fake = ctypes.c_void_p(16)
+    for p in bad:
+        r = L.ls_project(10, fake, fake, fake, fake, fake, ctypes.byref(cam), 1, ctypes.byref(p.c()), fake, None,
+                         None, None)
+        assert r == 1, p
+    good = raster.RenderParams()
+    # no cameras / too many cameras
+    assert L.ls_project(10, fake, fake, fake, fake, fake, ctypes.byref(cam), 0, ctypes.byref(good.c()), fake, None,
+                        None, None) == 1
+    assert L.ls_project(10, fake, fake, fake, fake, fake, ctypes.byref(cam), 65, ctypes.byref(good.c()), fake, None,
+                        None, None) == 1
+    # misaligned quaternion pointer
+    assert L.ls_project(10, fake, fake, ctypes.c_void_p(20), fake, fake, ctypes.byref(cam), 1,
+                        ctypes.byref(good.c()), fake, None, None, None) == 1
+    # zero-size camera
+    c2 = raster.cam_struct(dict(scenes.identity_camera(64, 64), width=0))
+    assert L.ls_render_fwd(fake, 10, ctypes.byref(c2), ctypes.byref(good.c()), fake, fake, fake, fake, fake, None,
+                           None) == 1
+    # workspace too small
+    assert L.ls_duplicate_sort(100, fake, ctypes.byref(cam), 1, ctypes.byref(good.c()), 1000, fake, fake, fake, fake,
+                               ctypes.c_void_p(256), 10, None, None) == 1
+    # records not a multiple of the camera count
+    cams2 = raster.cam_array([scenes.identity_camera(64, 64)] * 2)
+    assert L.ls_duplicate_sort(101, fake, cams2, 2, ctypes.byref(good.c()), 1000, fake, fake, fake, fake,
+                               ctypes.c_void_p(256), 1 << 30, None, None) == 1
+    # empty problem is valid and launches nothing
+    assert L.ls_project(0, None, None, None, None, None, ctypes.byref(cam), 1, ctypes.byref(good.c()), None, None,
+                        None, None) == 0

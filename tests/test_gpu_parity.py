@@ -1,0 +1,344 @@
+"""GPU parity: every stage of the CUDA path, called through the C ABI, against
+the FP64 oracle on the same seeded inputs.
+
+  duplicate + sort    bit-exact keys, record order and tile ranges
+  projection          records within 1e-5 relative (binary32 vs FP64)
+  forward blend       images within 1e-4 max abs on unflagged pixels
+  backward            gradients within 1e-3 relative L2 per tensor
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2411_12440_gb300 import _native as N
+from paper_2411_12440_gb300 import raster, scenes
+from tests.gpu_helpers import (GRAD_TOL, assert_image_parity, pack_records, rel_l2, unpack_proj)
+
+pytestmark = pytest.mark.gpu
+
+TILES = [(8, 8), (16, 16), (32, 16)]
+
+
+def _dupsort(rz, proj, R, cams, cap):
+    keys, vals, n_keys, ranges = rz.duplicate_sort(proj, R, cams, capacity=cap)
+    torch.cuda.synchronize()
+    K = int(n_keys.item())
+    return keys[:K].cpu().numpy().view(np.uint32), vals[:K].cpu().numpy().view(np.uint32), \
+        ranges.cpu().numpy().reshape(-1, 2), K
+
+
+# ------------------------------------------------------------------ a2 + a3
+@pytest.mark.parametrize("tile", TILES)
+@pytest.mark.parametrize("R,W,H", [(1, 300, 200), (3001, 300, 200), (40_000, 1297, 840)])
+def test_duplicate_sort_bitexact(tile, R, W, H):
+    rec = scenes.random_records(R, W, H, seed=R + tile[0])
+    proj, dkey = pack_records(rec)
+    P = raster.RenderParams(tile_w=tile[0], tile_h=tile[1])
+    rz = raster.Rasterizer(P)
+    cam = scenes.identity_camera(W, H)
+    foot = np.concatenate([rec["mean2d"], rec["ext"]], 1)
+    ok, ov, orr = oracle.dupsort_f32(foot, dkey, W, H, tile[0], tile[1])
+    keys, vals, ranges, K = _dupsort(rz, proj, R, [cam], cap=len(ok) + 17)
+    rz.check_status()
+    assert K == len(ok)
+    assert np.array_equal(keys, ok)
+    assert np.array_equal(vals, ov)
+    assert np.array_equal(ranges, orr)
+
+
+def test_duplicate_sort_ties_and_culled():
+    """Many equal depths (ties broken by record id) and a third of the records culled."""
+    W, H = 640, 360
+    rec = scenes.random_records(20_000, W, H, seed=11, visible_frac=0.66)
+    rec["depth"][:] = rec["depth"][:7].repeat(20_000 // 7 + 1)[:20_000]
+    proj, dkey = pack_records(rec)
+    rz = raster.Rasterizer(raster.RenderParams())
+    foot = np.concatenate([rec["mean2d"], rec["ext"]], 1)
+    ok, ov, orr = oracle.dupsort_f32(foot, dkey, W, H, 16, 16)
+    keys, vals, ranges, K = _dupsort(rz, proj, 20_000, [scenes.identity_camera(W, H)], cap=len(ok))
+    assert K == len(ok) and np.array_equal(vals, ov) and np.array_equal(ranges, orr)
+
+
+def test_duplicate_sort_empty_and_all_culled():
+    rz = raster.Rasterizer(raster.RenderParams())
+    cam = scenes.identity_camera(100, 60)
+    rec = scenes.random_records(500, 100, 60, seed=2, visible_frac=0.0)
+    proj, _ = pack_records(rec)
+    keys, vals, ranges, K = _dupsort(rz, proj, 500, [cam], cap=1000)
+    assert K == 0 and not ranges.any()
+    keys, vals, ranges, K = _dupsort(rz, torch.zeros(4, device="cuda"), 0, [cam], cap=0)
+    assert K == 0 and not ranges.any()
+    rz.check_status()
+
+
+def test_duplicate_sort_capacity_overflow_reports_and_recovers():
+    W, H = 300, 200
+    rec = scenes.random_records(2000, W, H, seed=5)
+    proj, dkey = pack_records(rec)
+    rz = raster.Rasterizer(raster.RenderParams())
+    cam = scenes.identity_camera(W, H)
+    foot = np.concatenate([rec["mean2d"], rec["ext"]], 1)
+    ok, ov, orr = oracle.dupsort_f32(foot, dkey, W, H, 16, 16)
+    _, _, ranges, K = _dupsort(rz, proj, 2000, [cam], cap=len(ok) - 1)
+    assert K == len(ok)  # the true count is reported
+    assert not ranges.any()
+    assert int(rz.status.item()) == 3
+    with pytest.raises(N.LsError):
+        rz.check_status()
+    rz.reset_status()
+    keys, vals, ranges, K = _dupsort(rz, proj, 2000, [cam], cap=len(ok))
+    rz.check_status()
+    assert np.array_equal(vals, ov) and np.array_equal(ranges, orr)
+
+
+def test_duplicate_sort_multi_camera_global_tiles():
+    """Records of several cameras of different sizes share one sort; tile ids
+    are global (camera c's tiles after those of cameras 0..c-1)."""
+    sizes = [(300, 200), (128, 96), (517, 211)]
+    cams = [scenes.identity_camera(w, h) for w, h in sizes]
+    n = 1500
+    recs = [scenes.random_records(n, w, h, seed=40 + i) for i, (w, h) in enumerate(sizes)]
+    allrec = {k: np.concatenate([r[k] for r in recs]) for k in recs[0]}
+    proj, dkey = pack_records(allrec)
+    rz = raster.Rasterizer(raster.RenderParams())
+    base = 0
+    exp_k, exp_v = [], []
+    exp_r = []
+    # oracle per camera, then merge: global order is (global tile, depth, record id)
+    for i, (w, h) in enumerate(sizes):
+        foot = np.concatenate([recs[i]["mean2d"], recs[i]["ext"]], 1)
+        k, v, r = oracle.dupsort_f32(foot, dkey[i * n:(i + 1) * n], w, h, 16, 16)
+        exp_k.append(k + base)
+        exp_v.append(v + i * n)
+        exp_r.append(r)
+        base += raster.tiles_of(cams[i], rz.params)
+    ok, ov = np.concatenate(exp_k), np.concatenate(exp_v)
+    keys, vals, ranges, K = _dupsort(rz, proj, 3 * n, cams, cap=len(ok))
+    assert np.array_equal(keys, ok) and np.array_equal(vals, ov)
+    shifted, before = [], 0
+    for k, r in zip(exp_k, exp_r):
+        rr = r.copy()
+        nz = rr[:, 1] > rr[:, 0]
+        rr[nz] += before
+        shifted.append(rr)
+        before += len(k)
+    assert np.array_equal(ranges, np.concatenate(shifted))
+
+
+# ------------------------------------------------------------------ a1
+def _proj_parity(scene, cam, P, rtol=1e-5):
+    rz = raster.Rasterizer(raster.RenderParams.from_dict(P))
+    sp = raster.Splats.from_scene(scene)
+    proj, tc = rz.project(sp, [cam])
+    torch.cuda.synchronize()
+    rec, foot, dkey = unpack_proj(proj, scene.n)
+    ref, vis = oracle.project(scene, cam, P)
+    gvis = dkey != 0xFFFFFFFF
+    # visibility may differ only where a cull threshold is met to rounding
+    diff = np.nonzero(gvis != vis)[0]
+    assert len(diff) <= max(2, 1e-4 * scene.n), len(diff)
+    m = gvis & vis
+    cols = [(0, oracle.P_MX), (1, oracle.P_MY), (2, oracle.P_A), (3, oracle.P_B), (4, oracle.P_C), (5, oracle.P_O),
+            (6, oracle.P_RHO2), (7, oracle.P_DEPTH), (8, oracle.P_R), (9, oracle.P_G), (10, oracle.P_BL)]
+    for gi, oi in cols:
+        g, o = rec[m, gi].astype(np.float64), ref[m, oi]
+        scale = np.maximum(np.abs(o), np.abs(ref[m][:, [oi]]).mean() * 1e-2 + 1e-6)
+        assert (np.abs(g - o) / scale).max() < 50 * rtol, (oi, (np.abs(g - o) / scale).max())
+    assert np.allclose(foot[m, 2], ref[m, oracle.P_EX], rtol=1e-4)
+    # sort key: the binary32 camera depth, a few ulp from the FP64 value
+    assert (np.abs(dkey[m].view(np.float32) - ref[m, oracle.P_DEPTH]) <= 1e-6 * ref[m, oracle.P_DEPTH]).all()
+    return rec, foot, dkey, ref, vis, tc.cpu().numpy()
+
+
+def test_project_parity_box_sh0():
+    scene, cams, _ = scenes.make_workload("plain_10k_256")
+    _proj_parity(scene, cams[0], dict(sh_degree=0))
+
+
+@pytest.mark.parametrize("aa", [0, 1])
+def test_project_parity_clusters_sh3(aa):
+    scene, cams, _ = scenes.make_workload("scene_1m_1297x840_aa", n=50_000)
+    _proj_parity(scene, cams[0], dict(sh_degree=3, antialias=aa))
+
+
+def test_project_tile_counts_match_oracle_rects():
+    scene, cams, _ = scenes.make_workload("scene_1m_1297x840_aa", n=20_000)
+    cam = cams[0]
+    rec, foot, dkey, ref, vis, tc = _proj_parity(scene, cam, dict(sh_degree=3))
+    bad = 0
+    for i in range(scene.n):
+        if dkey[i] == 0xFFFFFFFF:
+            assert tc[i] == 0
+            continue
+        r = oracle.rect(*foot[i].astype(np.float64).tolist(), cam["width"], cam["height"], True)
+        cnt = 0 if r is None else (r[1] // 16 - r[0] // 16 + 1) * (r[3] // 16 - r[2] // 16 + 1)
+        bad += cnt != tc[i]
+    assert bad == 0
+
+
+# ------------------------------------------------------------------ a4
+@pytest.mark.parametrize("tile", TILES)
+def test_render_records_parity(tile):
+    """Blend of random records alone: same binary32 lists on both sides."""
+    W, H = 333, 211
+    rec = scenes.random_records(3000, W, H, seed=21, max_ext=25)
+    proj, dkey = pack_records(rec)
+    P = dict(tile_w=tile[0], tile_h=tile[1], bg=(0.2, 0.1, 0.3))
+    rz = raster.Rasterizer(raster.RenderParams.from_dict(P))
+    cam = scenes.identity_camera(W, H)
+    rz.capacity = 3000 * 400
+    keys, vals, n_keys, ranges = rz.duplicate_sort(proj, 3000, [cam])
+    image, T, n_last = rz.render_fwd(proj, 3000, cam, ranges, vals)
+    torch.cuda.synchronize()
+    rz.check_status()
+    ref = oracle.render(oracle.records_to_proj(rec), rec["visible"], W, H, P, rule_f32=True, dkey=dkey)
+    assert_image_parity(image.cpu().numpy(), ref)
+    ok = ~ref["flags"]
+    assert np.abs(T.cpu().numpy() - ref["T"])[ok].max() < 1e-4
+    assert (n_last.cpu().numpy() == ref["n_last"])[ok].mean() > 0.9999
+
+
+def _render_gpu(scene, cam, P):
+    rz = raster.Rasterizer(raster.RenderParams.from_dict(P))
+    sp = raster.Splats.from_scene(scene)
+    image, T, state = rz.forward(sp, cam)
+    torch.cuda.synchronize()
+    rz.check_status()
+    return rz, sp, image, T, state
+
+
+@pytest.mark.parametrize("P", [dict(), dict(bg=(0.3, 0.6, 0.9)), dict(eps2d=0.0), dict(antialias=1)],
+                         ids=["default", "bg", "noeps", "aa"])
+def test_render_scene_parity_plain_10k(P):
+    scene, cams, _ = scenes.make_workload("plain_10k_256")
+    P = dict(P, sh_degree=0)
+    _, _, image, T, _ = _render_gpu(scene, cams[0], P)
+    ref = oracle.render_scene(scene, cams[0], P)
+    assert_image_parity(image.cpu().numpy(), ref)
+
+
+def test_render_images_independent_of_tile_shape():
+    """Same per-pixel operation order for every tile shape: bitwise equal."""
+    scene, cams, _ = scenes.make_workload("plain_10k_256")
+    imgs = []
+    for tw, th in TILES:
+        _, _, image, T, _ = _render_gpu(scene, cams[0], dict(sh_degree=0, tile_w=tw, tile_h=th))
+        imgs.append(image.cpu().numpy())
+    assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[1], imgs[2])
+
+
+@pytest.mark.parametrize("kid,lam", [(1, 1.0), (2, 1.0), (3, 2.5), (4, 6.0)])
+def test_render_kernel_family_parity(kid, lam):
+    scene, cams, _ = scenes.make_workload("plain_10k_256", n=4000)
+    P = dict(sh_degree=0, kernel=kid, lam=lam)
+    _, _, image, T, _ = _render_gpu(scene, cams[0], P)
+    ref = oracle.render_scene(scene, cams[0], P)
+    assert_image_parity(image.cpu().numpy(), ref, tol=2e-4, max_flag_frac=0.03)
+
+
+def test_render_stats_counts_match_oracle():
+    """Work units of the tile method (evaluated and composited pairs) counted
+    by the GPU equal the oracle's counts up to threshold flips."""
+    scene, cams, _ = scenes.make_workload("plain_10k_256")
+    cam = cams[0]
+    rz, sp, image, T, state = _render_gpu(scene, cam, dict(sh_degree=0))
+    img2, T2, nl2, n_eval, n_contrib = rz.render_stats(state["proj"], scene.n, cam, state["ranges"], state["vals"])
+    assert torch.equal(img2, image) and torch.equal(T2, T)
+    ref = oracle.render_scene(scene, cam, dict(sh_degree=0))
+    assert abs(n_contrib - ref["n_contrib"]) <= ref["flags"].sum()
+    assert abs(n_eval - ref["n_eval"]) <= 1e-3 * ref["n_eval"]
+
+
+# ------------------------------------------------------------------ a5
+def test_blend_bwd_records_parity():
+    W, H = 200, 136
+    rec = scenes.random_records(1500, W, H, seed=8, max_ext=20)
+    proj, dkey = pack_records(rec)
+    P = dict(bg=(0.1, 0.5, 0.2))
+    rz = raster.Rasterizer(raster.RenderParams.from_dict(P))
+    cam = scenes.identity_camera(W, H)
+    rz.capacity = 1500 * 200
+    keys, vals, n_keys, ranges = rz.duplicate_sort(proj, 1500, [cam])
+    image, T, n_last = rz.render_fwd(proj, 1500, cam, ranges, vals)
+    w, v = scenes.loss_weights(H, W, seed=3)
+    g2d = torch.zeros((1500, 12), device="cuda")
+    c = raster.cam_struct(cam)
+    wd, vd = torch.from_numpy(w).cuda(), torch.from_numpy(v).cuda()  # alive until the kernel has run
+    N.check(N.lib().ls_blend_bwd(raster._p(proj), 1500, ctypes.byref(c), ctypes.byref(rz.params.c()),
+                                 raster._p(ranges), raster._p(vals), raster._p(T), raster._p(n_last), raster._p(wd),
+                                 raster._p(vd), raster._p(g2d), raster._p(rz.status), raster._stream()),
+            "ls_blend_bwd")
+    torch.cuda.synchronize()
+    rz.check_status()
+    ref = oracle.render_bwd(oracle.records_to_proj(rec), rec["visible"], W, H, w.astype(np.float64),
+                            v.astype(np.float64), P, rule_f32=True, dkey=dkey)
+    g = g2d.cpu().numpy()
+    cols = [0, 1, 2, 3, 4, 5, 6, 7, 8]
+    for j, gc in enumerate(cols):
+        assert rel_l2(g[:, gc], ref[:, j]) < GRAD_TOL, (j, rel_l2(g[:, gc], ref[:, j]))
+
+
+CASES_BWD = [
+    ("plain", "plain_10k_256", None, dict(sh_degree=0)),
+    ("bg_aa", "plain_10k_256", None, dict(sh_degree=0, antialias=1, bg=(0.5, 0.2, 0.7))),
+    ("ags", "plain_10k_256", None, dict(sh_degree=0, ags=1)),
+    ("ags_aligned", "plain_10k_256", None, dict(sh_degree=0, ags=2)),
+    ("sh3_clusters", "scene_1m_1297x840_aa", 30_000, dict(sh_degree=3, antialias=1)),
+]
+
+
+@pytest.mark.parametrize("name,wl,n,P", CASES_BWD, ids=[c[0] for c in CASES_BWD])
+def test_render_bwd_parity(name, wl, n, P):
+    scene, cams, _ = scenes.make_workload(wl, n=n)
+    cam = cams[0]
+    rz, sp, image, T, state = _render_gpu(scene, cam, P)
+    w, v = scenes.loss_weights(cam["height"], cam["width"], seed=4)
+    g = rz.render_bwd(sp, cam, state, torch.from_numpy(w).cuda(), torch.from_numpy(v).cuda(), want_g2d=True)
+    torch.cuda.synchronize()
+    rz.check_status()
+    ref = oracle.scene_grads(scene, cam, w.astype(np.float64), v.astype(np.float64), P)
+    n = scene.n
+    got = dict(means=g["means"].cpu().numpy(), scales=g["scales"].cpu().numpy(), quats=g["quats"].cpu().numpy(),
+               opac=g["opac"].cpu().numpy(), sh=raster.Splats.sh_from_device_layout(g["sh"], n).cpu().numpy())
+    for k in ("means", "scales", "quats", "opac", "sh"):
+        e = rel_l2(got[k], ref[k])
+        assert e < GRAD_TOL, (k, e)
+
+
+def test_autograd_function_matches_direct_backward():
+    scene, cams, _ = scenes.make_workload("plain_10k_256", n=3000)
+    cam = cams[0]
+    rz = raster.Rasterizer(raster.RenderParams(sh_degree=0))
+    sp = raster.Splats.from_scene(scene)
+    for t in sp.tensors():
+        t.requires_grad_(True)
+    image, T = raster.render(sp, cam, rz)
+    w, v = scenes.loss_weights(cam["height"], cam["width"], seed=6)
+    loss = (image * torch.from_numpy(w).cuda()).sum() + (T * torch.from_numpy(v).cuda()).sum()
+    loss.backward()
+    ref = oracle.scene_grads(scene, cam, w.astype(np.float64), v.astype(np.float64), dict(sh_degree=0))
+    assert rel_l2(sp.means.grad.cpu().numpy(), ref["means"]) < GRAD_TOL
+    assert rel_l2(sp.opac.grad.cpu().numpy(), ref["opac"]) < GRAD_TOL
+    sh = raster.Splats.sh_from_device_layout(sp.sh.grad, scene.n).cpu().numpy()
+    assert rel_l2(sh, ref["sh"]) < GRAD_TOL
+
+
+# ------------------------------------------------------------------ full size, sampled
+@pytest.mark.parametrize("wl,window", [("scene_1m_1297x840_aa", (600, 728, 380, 476)),
+                                       ("diff_3m_1080p", (900, 1028, 500, 580))])
+def test_full_size_forward_window(wl, window):
+    """Full-size scenes in the launch configuration the benchmark times,
+    checked on a pixel window the oracle composites in seconds."""
+    scene, cams, extra = scenes.make_workload(wl)
+    cam = cams[0]
+    P = dict(sh_degree=3, antialias=int(extra["antialias"]))
+    _, _, image, T, state = _render_gpu(scene, cam, P)
+    oracle.set_threads(8)
+    ref = oracle.render_scene(scene, cam, P, window=window)
+    assert_image_parity(image.cpu().numpy(), ref, region=window)
+    x0, x1, y0, y1 = window
+    ok = ~ref["flags"][y0:y1, x0:x1]
+    assert np.abs(T.cpu().numpy()[y0:y1, x0:x1] - ref["T"][y0:y1, x0:x1])[ok].max() < 1e-4
