@@ -86,10 +86,12 @@ typedef struct {
 /* Projected-record buffer.  For n primitives seen by n_cams cameras there are
  * R = n_cams * n records; record r = cam * n + i.  The buffer holds three
  * consecutive planes, 68 bytes per record (ls_proj_bytes):
- *   rec  [R][12] float at byte 0:        {mx, my, a, b}, {c, o_eff, rho^2, depth}, {r, g, b, 0}
+ *   rec  [R][12] float at byte 0:        {mx, my, l00, l01}, {l11, o_eff, rho^2, depth}, {r, g, b, 0}
  *        screen centre mu' (pixel units, pixel (px,py) covers [px,px+1)x[py,py+1)),
- *        conic A = (Sigma_2D + eps2d I)^-1 = [[a, b], [b, c]], effective opacity,
- *        squared support radius in Mahalanobis units, camera depth, colour;
+ *        the conic A = (Sigma_2D + eps2d I)^-1 = [[a, b], [b, c]] as its upper
+ *        Cholesky factor L = [[l00, l01], [0, l11]], A = L^T L (so D^2 = |L d|^2
+ *        is a sum of squares), effective opacity, squared support radius in
+ *        Mahalanobis units, camera depth, colour;
  *   foot [R][4] float at byte 48*R:      {mx, my, ex, ey} half extents of the support box;
  *   dkey [R] uint32 at byte 64*R:        binary32 bits of depth, 0xFFFFFFFF when culled.
  * Fields of culled records other than dkey are unspecified. */
@@ -153,7 +155,9 @@ ls_status ls_render_stats(const void* proj, int64_t n_records, const ls_camera* 
  * (Eq. 6); with params->ags the kernel-derivative path is scaled by w(D)
  * (Eq. 13-14).  grad_image [H][W][3]; grad_t [H][W] or NULL.  g2d [R][12]
  * float is ACCUMULATED into (zero it first): {gmx, gmy, ga, gb}, {gc, go,
- * gr, gg}, {gb, 0, 0, 0}. */
+ * gr, gg}, {gb, 0, 0, 0}, where ga, gb, gc are the gradients with respect to
+ * the conic entries a, b, c of A (b counted once, as in d^T A d =
+ * a dx^2 + 2 b dx dy + c dy^2), whatever factor the record stores. */
 ls_status ls_blend_bwd(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
                        const int32_t* tile_ranges, const uint32_t* vals, const float* t_final,
                        const int32_t* n_last, const float* grad_image, const float* grad_t, float* g2d,

@@ -234,9 +234,11 @@ def records_to_proj(rec):
     p = np.zeros((n, NP))
     p[:, P_MX] = rec["mean2d"][:, 0]
     p[:, P_MY] = rec["mean2d"][:, 1]
-    p[:, P_A] = rec["conic"][:, 0]
-    p[:, P_B] = rec["conic"][:, 1]
-    p[:, P_C] = rec["conic"][:, 2]
+    # inverse covariance A = L^T L of the stored factor L = [[l00, l01], [0, l11]]
+    l00, l01, l11 = (rec["chol"][:, k].astype(np.float64) for k in range(3))
+    p[:, P_A] = l00 * l00
+    p[:, P_B] = l00 * l01
+    p[:, P_C] = l01 * l01 + l11 * l11
     p[:, P_O] = rec["opac"]
     p[:, P_RHO2] = rec["rho2"]
     p[:, P_DEPTH] = rec["depth"]

@@ -27,11 +27,14 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 }
 
 // One (pixel, record) pair, with every rounding explicit so that the forward
-// and the backward take bit-identical skip decisions: q = d^T A d, skip when
-// q > rho^2; D = sqrt(q); alpha = min(alpha_max, o f(D / lambda)); skip when
-// alpha < alpha_min.
+// and the backward take bit-identical skip decisions.  The conic is stored as
+// its upper Cholesky factor L (A = L^T L), so q = d^T A d = |L d|^2 =
+// (l00 dx + l01 dy)^2 + (l11 dy)^2 is a sum of squares: no cancellation even
+// for needle-shaped footprints, where a dx^2 + 2 b dx dy + c dy^2 adds terms
+// thousands of times larger than q.  Skip when q > rho^2; D = sqrt(q);
+// alpha = min(alpha_max, o f(D / lambda)); skip when alpha < alpha_min.
 struct PairEval {
-  float dx, dy, q, D, xk, f, araw, alpha;
+  float dx, dy, e1, e2, q, D, xk, f, araw, alpha;
 };
 
 template <int KID>
@@ -39,8 +42,9 @@ __device__ __forceinline__ bool pair_alpha(float x, float y, const float4& a, co
                                            PairEval& e) {
   e.dx = __fsub_rn(x, a.x);
   e.dy = __fsub_rn(y, a.y);
-  const float t = __fmaf_rn(a.z, e.dx, __fmul_rn(__fmul_rn(2.f, a.w), e.dy));
-  e.q = __fmaf_rn(e.dx, t, __fmul_rn(__fmul_rn(bb.x, e.dy), e.dy));
+  e.e1 = __fmaf_rn(a.z, e.dx, __fmul_rn(a.w, e.dy));
+  e.e2 = __fmul_rn(bb.x, e.dy);
+  e.q = __fmaf_rn(e.e1, e.e1, __fmul_rn(e.e2, e.e2));
   if (e.q > bb.z) return false;
   e.D = sqrt_approx(e.q);
   e.xk = __fmul_rn(e.D, P.inv_lambda);
@@ -61,8 +65,8 @@ __global__ void __launch_bounds__(512) blend_fwd_kernel(const float4* __restrict
                                                         unsigned long long* stats) {
   extern __shared__ float4 smem[];
   const int B = blockDim.x;
-  float4* s_a = smem;          // {mx, my, a, b}
-  float4* s_b = smem + B;      // {c, o, rho2, depth}
+  float4* s_a = smem;          // {mx, my, l00, l01}
+  float4* s_b = smem + B;      // {l11, o, rho2, depth}
   float4* s_c = smem + 2 * B;  // {r, g, b, -}
   const int tile = blockIdx.x;
   const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
@@ -234,8 +238,9 @@ __global__ void __launch_bounds__(512) blend_bwd_kernel(const float4* __restrict
               if (P.ags == 1) gD *= __expf(-D * D);
               else if (P.ags == 2) gD *= __expf(-xk * xk);
               const float gq = D > 0.f ? 0.5f * gD / D : 0.f;
-              v[0] = -2.f * gq * (a.z * dx + a.w * dy);
-              v[1] = -2.f * gq * (a.w * dx + bb.x * dy);
+              // A d = L^T (L d)
+              v[0] = -2.f * gq * (a.z * e.e1);
+              v[1] = -2.f * gq * (a.w * e.e1 + bb.x * e.e2);
               v[2] = gq * dx * dx;
               v[3] = 2.f * gq * dx * dy;
               v[4] = gq * dy * dy;

@@ -226,13 +226,17 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(int n, const float* __
     col[ch] = fmaxf(v, 0.f);
   }
   float sxx = s.S2[0] + P.eps2d, syy = s.S2[2] + P.eps2d, sxy = s.S2[1];
-  float idet = 1.f / s.det;
   float itz = 1.f / s.t[2];
   float mx = cam.fx * s.t[0] * itz + cam.cx;
   float my = cam.fy * s.t[1] * itz + cam.cy;
   float ex = rho * sqrtf(sxx), ey = rho * sqrtf(syy);
-  out.rec[3 * r] = make_float4(mx, my, syy * idet, -sxy * idet);
-  out.rec[3 * r + 1] = make_float4(sxx * idet, oe, rho * rho, s.t[2]);
+  // conic A = Sigma_d^-1 as its upper Cholesky factor, from the accurate det:
+  // l00 = sqrt(syy / det), l01 = -sxy / sqrt(det syy), l11 = 1 / sqrt(syy)
+  float l00 = sqrtf(syy / s.det);
+  float l01 = -sxy / sqrtf(s.det * syy);
+  float l11 = 1.f / sqrtf(syy);
+  out.rec[3 * r] = make_float4(mx, my, l00, l01);
+  out.rec[3 * r + 1] = make_float4(l11, oe, rho * rho, s.t[2]);
   out.rec[3 * r + 2] = make_float4(col[0], col[1], col[2], 0.f);
   out.foot[r] = make_float4(mx, my, ex, ey);
   out.dkey[r] = __float_as_uint(s.t[2]);

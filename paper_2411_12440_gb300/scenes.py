@@ -220,30 +220,29 @@ def make_workload(name, n=None, seed=None):
 # --------------------------------------------------------------------------
 
 def random_records(n, width, height, seed, visible_frac=0.9, max_ext=40.0):
-    """Random screen-space footprints: centre, axis half-extent, conic entries,
-    effective opacity, squared cutoff, depth and colour, all float32.  Depths
-    are drawn from a small set of values so ties are frequent."""
+    """Random screen-space footprints, all float32: centre, half extents of
+    the support box, the upper-triangular factor (l00, l01, l11) of an
+    ellipse's inverse covariance, effective opacity, squared cutoff, depth
+    and colour.  The ellipse has axis std (ex, ey) / 2.5 and correlation
+    cc, so a cutoff up to 2.5 stays inside the box.  Depths come from a
+    small set of values so ties are frequent."""
     rng = np.random.default_rng(seed)
     mx = rng.uniform(-0.2 * width, 1.2 * width, n)
     my = rng.uniform(-0.2 * height, 1.2 * height, n)
     ex = np.exp(rng.uniform(math.log(0.3), math.log(max_ext), n))
     ey = np.exp(rng.uniform(math.log(0.3), math.log(max_ext), n))
-    # conic of an axis-aligned-ish ellipse with a random shear
     sx = ex / 2.5
     sy = ey / 2.5
     rho = rng.uniform(0.4, 1.0, n)
     cc = rng.uniform(-0.9, 0.9, n)
-    det = (sx * sx) * (sy * sy) * (1 - cc * cc)
-    a = (sy * sy) / det
-    c = (sx * sx) / det
-    b = -(cc * sx * sy) / det
+    sq = np.sqrt(1 - cc * cc)
+    chol = np.stack([1.0 / (sx * sq), -cc / (sy * sq), 1.0 / sy], 1)
     o = rng.uniform(0.05, 0.99, n)
     depth = rng.choice(np.linspace(0.5, 50.0, 997), size=n)
     rgb = rng.uniform(0, 1, (n, 3))
     vis = rng.uniform(0, 1, n) < visible_frac
-    return dict(mean2d=_f32(np.stack([mx, my], 1)), ext=_f32(np.stack([ex, ey], 1)),
-                conic=_f32(np.stack([a, b, c], 1)), opac=_f32(o), rho2=_f32((2.5 * rho) ** 2),
-                depth=_f32(depth), rgb=_f32(rgb), visible=vis)
+    return dict(mean2d=_f32(np.stack([mx, my], 1)), ext=_f32(np.stack([ex, ey], 1)), chol=_f32(chol),
+                opac=_f32(o), rho2=_f32((2.5 * rho) ** 2), depth=_f32(depth), rgb=_f32(rgb), visible=vis)
 
 
 def loss_weights(height, width, seed):

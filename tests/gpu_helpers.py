@@ -15,9 +15,9 @@ def pack_records(rec, device="cuda"):
     R = rec["opac"].shape[0]
     r12 = np.zeros((R, 12), np.float32)
     r12[:, 0:2] = rec["mean2d"]
-    r12[:, 2] = rec["conic"][:, 0]
-    r12[:, 3] = rec["conic"][:, 1]
-    r12[:, 4] = rec["conic"][:, 2]
+    r12[:, 2] = rec["chol"][:, 0]
+    r12[:, 3] = rec["chol"][:, 1]
+    r12[:, 4] = rec["chol"][:, 2]
     r12[:, 5] = rec["opac"]
     r12[:, 6] = rec["rho2"]
     r12[:, 7] = rec["depth"]
@@ -69,3 +69,9 @@ def assert_image_parity(img, ref, region=None, tol=IMG_TOL, max_flag_frac=0.01):
     if nflag:
         assert err[flags].max() <= 2 / 255 + tol
     return float(err[ok].max()), nflag
+
+
+def conic_of(rec12):
+    """(a, b, c) of A = L^T L from the stored factor (l00, l01, l11), FP64."""
+    l00, l01, l11 = (rec12[:, k].astype(np.float64) for k in (2, 3, 4))
+    return np.stack([l00 * l00, l00 * l01, l01 * l01 + l11 * l11], 1)
