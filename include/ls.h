@@ -187,6 +187,34 @@ ls_status ls_render_bwd(int32_t n, const float* means, const float* scales, cons
                         float* g_sh, float* g2d_out, void* workspace, size_t ws_bytes, int32_t* status_dev,
                         void* stream);
 
+/* ls_duplicate_sort without a caller-supplied workspace, for callers that
+ * cannot allocate device memory themselves: a plugin running inside a host
+ * application that owns every device allocation, a real-time loop that must
+ * not allocate, or a small C program that links only this library and keeps
+ * no allocator of its own.  The paper has no counterpart; this is a packaging
+ * choice.
+ *
+ * The scratch lives in one file-scope device array of LS_NOALLOC_SCRATCH_BYTES
+ * that every GPU which loads the library holds until the process exits.  The
+ * caller still passes (and owns) proj, keys, vals, n_keys_dev, tile_ranges and
+ * status_dev, exactly as for ls_duplicate_sort, and gets the same results.
+ * Limits: n_records <= LS_NOALLOC_MAX_RECORDS, key_capacity <=
+ * LS_NOALLOC_MAX_KEYS, and the scratch that ls_duplicate_sort_workspace asks
+ * for must fit the array; anything larger returns LS_ERR_UNSUPPORTED before
+ * any work is enqueued.  Other argument errors are those of ls_duplicate_sort.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture begins.  Every call uses the same array: the call clears what must
+ * start at zero, and calls whose work overlaps on the GPU (other streams,
+ * other threads) race on it, so serialise them.  No cudaMalloc or cudaFree,
+ * and no allocating library routine, is called. */
+#define LS_NOALLOC_MAX_RECORDS 65536
+#define LS_NOALLOC_MAX_KEYS 524288
+#define LS_NOALLOC_SCRATCH_BYTES (8u << 20)
+ls_status ls_duplicate_sort_noalloc(int64_t n_records, const void* proj, const ls_camera* cams, int32_t n_cams,
+                                    const ls_params* params, int64_t key_capacity, uint32_t* keys, uint32_t* vals,
+                                    int64_t* n_keys_dev, int32_t* tile_ranges, int32_t* status_dev, void* stream);
+
 /* Text of a status code (static storage). */
 const char* ls_status_string(int32_t status);
 

@@ -50,6 +50,7 @@ PROTOTYPES = {
     "ls_project": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _I32, _PP, _P, _P, _P, _P]),
     "ls_duplicate_sort_workspace": (_SZ, [_I64, _I64, _I32]),
     "ls_duplicate_sort": (_I32, [_I64, _P, _PC, _I32, _PP, _I64, _P, _P, _P, _P, _P, _SZ, _P, _P]),
+    "ls_duplicate_sort_noalloc": (_I32, [_I64, _P, _PC, _I32, _PP, _I64, _P, _P, _P, _P, _P, _P]),
     "ls_render_fwd": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _P, _P, _P, _P]),
     "ls_render_stats": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ls_blend_bwd": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
