@@ -212,8 +212,10 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--prims", type=int, default=None,
+                    help="override the primitive count (same recipe; for small profiling cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -229,7 +231,7 @@ def main():
     ws, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    scene, cams, extra = scenes.make_workload(WORKLOAD)
+    scene, cams, extra = scenes.make_workload(WORKLOAD, n=args.prims)
     cam = cams[0]
     P = raster.RenderParams(sh_degree=3, antialias=int(extra["antialias"]))
     rz = raster.Rasterizer(P, device=dev)
@@ -389,7 +391,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "prims": R, "width": W, "height": H, "sh_degree": 3,
+            "config": {"workload": WORKLOAD if args.prims is None else "%s (prims=%d)" % (WORKLOAD, R), "prims": R,
+                   "width": W, "height": H, "sh_degree": 3,
                        "tile": "%dx%d" % (P.tile_w, P.tile_h), "l2": "inputs larger than L2 (708 MB of parameters)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "fwd_fps": ws * 1e3 / fwd_ms, "fwd_ms": fwd_ms,

@@ -2,18 +2,20 @@
 // adjoint (Sec. 3.1 Eq. 6; kernel of Sec. 3.2 Eq. 11 with the alignment of
 // Sec. 3.3.1 Eq. 12; adaptive gradient scaling of Sec. 3.3.2 Eq. 13-14).
 //
-// One CTA per tile, one thread per pixel.  The tile's sorted record ids are
-// walked in batches of one record per thread: each thread gathers one 48-byte
-// record into shared memory, then every pixel reads the batch from shared
-// memory (broadcast reads), so each record is fetched from L2/HBM once per
-// tile and reused by all of the tile's pixels.
+// One CTA per tile; each thread owns a 1 x PPT strip of pixels in one row, so
+// one shared-memory read of a record serves PPT pixels and the per-record
+// terms that depend only on the row (dy, l01 dy, l11 dy) are computed once.
+// The tile's sorted record ids are walked in batches: the threads gather the
+// batch's 48-byte records into shared memory (each record is fetched from
+// L2/HBM once per tile), then every thread reads them as broadcasts.
 //
 // Backward: each pixel restarts from its checkpoint (T_final, n_last) and
 // walks its list back to front, recovering T before each entry as
-// T / (1 - alpha).  Per record, a warp that has any contributing pixel sums
-// the nine gradient terms with xor-shuffles, lane 0 adds them into a per-CTA
-// shared-memory slot, and after the batch one set of vector atomics per
-// (record, CTA) lands in global memory.
+// T / (1 - alpha).  Each thread first sums its PPT pixels' nine gradient
+// terms; a warp with any contributing pixel then reduce-scatters the nine sums
+// (14 shuffles instead of 45: eight values end in eight lane groups), those
+// lanes add into a per-CTA shared-memory slot, and after the batch one set of
+// float4 atomics per (record, CTA) lands in global memory.
 #include "kernels.h"
 
 namespace ls {
@@ -26,244 +28,331 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
-// One (pixel, record) pair, with every rounding explicit so that the forward
-// and the backward take bit-identical skip decisions.  The conic is stored as
-// its upper Cholesky factor L (A = L^T L), so q = d^T A d = |L d|^2 =
-// (l00 dx + l01 dy)^2 + (l11 dy)^2 is a sum of squares: no cancellation even
-// for needle-shaped footprints, where a dx^2 + 2 b dx dy + c dy^2 adds terms
-// thousands of times larger than q.  Skip when q > rho^2; D = sqrt(q);
-// alpha = min(alpha_max, o f(D / lambda)); skip when alpha < alpha_min.
-struct PairEval {
-  float dx, dy, e1, e2, q, D, xk, f, araw, alpha;
-};
-
-template <int KID>
-__device__ __forceinline__ bool pair_alpha(float x, float y, const float4& a, const float4& bb, const ParDev& P,
-                                           PairEval& e) {
-  e.dx = __fsub_rn(x, a.x);
-  e.dy = __fsub_rn(y, a.y);
-  e.e1 = __fmaf_rn(a.z, e.dx, __fmul_rn(a.w, e.dy));
-  e.e2 = __fmul_rn(bb.x, e.dy);
-  e.q = __fmaf_rn(e.e1, e.e1, __fmul_rn(e.e2, e.e2));
-  if (e.q > bb.z) return false;
-  e.D = sqrt_approx(e.q);
-  e.xk = __fmul_rn(e.D, P.inv_lambda);
-  e.f = kern_f<KID>(e.xk);
-  e.araw = __fmul_rn(bb.y, e.f);
-  e.alpha = fminf(P.alpha_max, e.araw);
-  return e.alpha >= P.alpha_min;
+// The squared Mahalanobis distance of pixel (x, y) to record (a, bb), with
+// every rounding explicit so that the forward and the backward compute the
+// same bits.  The conic is stored as its upper Cholesky factor L (A = L^T L),
+// so q = |L d|^2 = (l00 dx + l01 dy)^2 + (l11 dy)^2 is a sum of squares: no
+// cancellation even for needle-shaped footprints.  Row terms (depending on y
+// only) are passed in: l01dy = l01 dy, e2s = (l11 dy)^2.
+__device__ __forceinline__ float pair_q(float x, float mx, float l00, float l01dy, float e2s, float& dx, float& e1) {
+  dx = __fsub_rn(x, mx);
+  e1 = __fmaf_rn(l00, dx, l01dy);
+  return __fmaf_rn(e1, e1, e2s);
 }
 
-// COUNT = true also tallies the work units of the tile method: evaluated
-// pairs (per tile, the pixels times the entries walked until the tile's last
-// pixel finished) and composited pairs; stats[0], stats[1] (uint64).
-template <int KID, bool COUNT>
-__global__ void __launch_bounds__(512) blend_fwd_kernel(const float4* __restrict__ rec, const CamDev cam,
-                                                        const ParDev P, const int2* __restrict__ ranges,
-                                                        const uint32_t* __restrict__ vals, float* __restrict__ image,
-                                                        float* __restrict__ t_final, int32_t* __restrict__ n_last,
-                                                        unsigned long long* stats) {
-  extern __shared__ float4 smem[];
-  const int B = blockDim.x;
-  float4* s_a = smem;          // {mx, my, l00, l01}
-  float4* s_b = smem + B;      // {l11, o, rho2, depth}
-  float4* s_c = smem + 2 * B;  // {r, g, b, -}
-  const int tile = blockIdx.x;
-  const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-  const int px = tx * P.tile_w + (int)threadIdx.x % P.tile_w;
-  const int py = ty * P.tile_h + (int)threadIdx.x / P.tile_w;
-  const bool inside = px < cam.W && py < cam.H;
-  const float x = (float)px + 0.5f, y = (float)py + 0.5f;
-  const int2 rg = ranges[cam.tile_base + tile];
-  const int n = rg.y - rg.x;
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  int last = 0;
-  bool done = !inside;
-  int stop = n;         // COUNT: index where this pixel finished
-  int composited = 0;   // COUNT
+// alpha of a pair inside the support: min(alpha_max, o f(D / lambda)).
+template <int KID>
+__device__ __forceinline__ void pair_alpha(float q, float o, const ParDev& P, float& D, float& xk, float& f,
+                                           float& araw, float& alpha) {
+  D = sqrt_approx(q);
+  xk = __fmul_rn(D, P.inv_lambda);
+  f = kern_f<KID>(xk);
+  araw = __fmul_rn(o, f);
+  alpha = fminf(P.alpha_max, araw);
+}
+
+// Where a tile lives: pixel origin, image size, its key range, and the base of
+// its camera's image in the output arrays.
+struct TileJob {
+  int x0, y0, W, H;
+  int2 rg;
+  size_t pix_base;
+};
+
+// ---------------------------------------------------------------- forward
+template <int KID, int PPT, bool COUNT>
+__device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
+                                         const ParDev& P, const TileJob& J, float4* s_a, float4* s_b, float4* s_c,
+                                         int B, float* __restrict__ image, float* __restrict__ t_final,
+                                         int32_t* __restrict__ n_last, unsigned long long* stats) {
+  const int sx = P.tile_w / PPT;
+  const int lr = (int)threadIdx.x / sx, lc = ((int)threadIdx.x % sx) * PPT;
+  const int py = J.y0 + lr, px0 = J.x0 + lc;
+  const float y = (float)py + 0.5f;
+  float xs[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+  int last[PPT], stop[PPT], comp[PPT];
+  unsigned done = 0;
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    xs[p] = (float)(px0 + p) + 0.5f;
+    T[p] = 1.f;
+    C0[p] = C1[p] = C2[p] = 0.f;
+    last[p] = 0;
+    comp[p] = 0;
+    if (!(px0 + p < J.W && py < J.H)) done |= 1u << p;
+  }
+  const unsigned all = (1u << PPT) - 1u;
+  const int n = J.rg.y - J.rg.x;
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) stop[p] = n;
   for (int b0 = 0; b0 < n; b0 += B) {
-    if (__syncthreads_and(done)) break;
-    const int k = b0 + (int)threadIdx.x;
-    if (k < n) {
-      const uint32_t id = vals[rg.x + k];
-      s_a[threadIdx.x] = rec[3 * (size_t)id];
-      s_b[threadIdx.x] = rec[3 * (size_t)id + 1];
-      s_c[threadIdx.x] = rec[3 * (size_t)id + 2];
+    if (__syncthreads_and(done == all)) break;
+    const int cnt = min(B, n - b0);
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      const uint32_t id = vals[J.rg.x + b0 + k];
+      s_a[k] = rec[3 * (size_t)id];
+      s_b[k] = rec[3 * (size_t)id + 1];
+      s_c[k] = rec[3 * (size_t)id + 2];
     }
     __syncthreads();
-    const int cnt = min(B, n - b0);
-    if (!done) {
+    if (done != all) {
       for (int j = 0; j < cnt; ++j) {
-        PairEval e;
-        if (!pair_alpha<KID>(x, y, s_a[j], s_b[j], P, e)) continue;
-        const float alpha = e.alpha;
-        const float Tn = T * (1.f - alpha);
-        if (Tn < P.t_min) {
-          done = true;
-          if (COUNT) stop = b0 + j;
-          break;
+        const float4 a = s_a[j];   // {mx, my, l00, l01}
+        const float4 bb = s_b[j];  // {l11, o, rho2, depth}
+        const float dy = __fsub_rn(y, a.y);
+        const float l01dy = __fmul_rn(a.w, dy);
+        const float e2 = __fmul_rn(bb.x, dy);
+        const float e2s = __fmul_rn(e2, e2);
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+          float dx, e1;
+          const float q = pair_q(xs[p], a.x, a.z, l01dy, e2s, dx, e1);
+          if (((done >> p) & 1u) || q > bb.z) continue;
+          float D, xk, f, araw, alpha;
+          pair_alpha<KID>(q, bb.y, P, D, xk, f, araw, alpha);
+          if (alpha < P.alpha_min) continue;
+          const float Tn = T[p] * (1.f - alpha);
+          if (Tn < P.t_min) {
+            done |= 1u << p;
+            if (COUNT) stop[p] = b0 + j;
+            continue;
+          }
+          const float4 c = s_c[j];
+          const float w = alpha * T[p];
+          C0[p] += c.x * w;
+          C1[p] += c.y * w;
+          C2[p] += c.z * w;
+          T[p] = Tn;
+          last[p] = b0 + j + 1;
+          if (COUNT) ++comp[p];
         }
-        const float4 c = s_c[j];
-        const float w = alpha * T;
-        C0 += c.x * w;
-        C1 += c.y * w;
-        C2 += c.z * w;
-        T = Tn;
-        last = b0 + j + 1;
-        if (COUNT) ++composited;
+        if (done == all) break;
       }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    if (px0 + p < J.W && py < J.H) {
+      const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p;
+      image[3 * pi] = C0[p] + T[p] * P.bg[0];
+      image[3 * pi + 1] = C1[p] + T[p] * P.bg[1];
+      image[3 * pi + 2] = C2[p] + T[p] * P.bg[2];
+      t_final[pi] = T[p];
+      n_last[pi] = last[p];
     }
   }
   if (COUNT) {
     __shared__ int s_emax, s_npix;
     __shared__ unsigned long long s_contrib;
+    __syncthreads();
     if (threadIdx.x == 0) {
       s_emax = 0;
       s_npix = 0;
       s_contrib = 0;
     }
     __syncthreads();
-    if (inside) {
-      atomicMax(&s_emax, stop < n ? stop + 1 : n);
-      atomicAdd(&s_npix, 1);
-      atomicAdd(&s_contrib, (unsigned long long)composited);
+    int emax = 0, npix = 0, cc = 0;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      if (px0 + p < J.W && py < J.H) {
+        emax = max(emax, stop[p] < n ? stop[p] + 1 : n);
+        ++npix;
+        cc += comp[p];
+      }
     }
+    atomicMax(&s_emax, emax);
+    atomicAdd(&s_npix, npix);
+    atomicAdd(&s_contrib, (unsigned long long)cc);
     __syncthreads();
     if (threadIdx.x == 0) {
       atomicAdd(&stats[0], (unsigned long long)s_emax * (unsigned long long)s_npix);
       atomicAdd(&stats[1], s_contrib);
     }
   }
-  if (inside) {
-    const size_t p = (size_t)py * cam.W + px;
-    image[3 * p] = C0 + T * P.bg[0];
-    image[3 * p + 1] = C1 + T * P.bg[1];
-    image[3 * p + 2] = C2 + T * P.bg[2];
-    t_final[p] = T;
-    n_last[p] = last;
-  }
 }
 
-template <int KID>
-__global__ void __launch_bounds__(512) blend_bwd_kernel(const float4* __restrict__ rec, const CamDev cam,
+template <int KID, int PPT, bool COUNT>
+__global__ void __launch_bounds__(128) blend_fwd_kernel(const float4* __restrict__ rec, const CamDev cam,
                                                         const ParDev P, const int2* __restrict__ ranges,
-                                                        const uint32_t* __restrict__ vals,
-                                                        const float* __restrict__ t_final,
-                                                        const int32_t* __restrict__ n_last,
-                                                        const float* __restrict__ grad_image,
-                                                        const float* __restrict__ grad_t, float* __restrict__ g2d) {
+                                                        const uint32_t* __restrict__ vals, float* __restrict__ image,
+                                                        float* __restrict__ t_final, int32_t* __restrict__ n_last,
+                                                        unsigned long long* stats) {
   extern __shared__ float4 smem[];
-  const int B = blockDim.x;
-  float4* s_a = smem;
-  float4* s_b = smem + B;
-  float4* s_c = smem + 2 * B;
-  float* s_acc = reinterpret_cast<float*>(smem + 3 * B);  // [B][9]
-  uint32_t* s_id = reinterpret_cast<uint32_t*>(s_acc + 9 * B);
-  int* s_touch = reinterpret_cast<int*>(s_id + B);
-  __shared__ int s_max;
-
+  const int B = 4 * blockDim.x;
   const int tile = blockIdx.x;
-  const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-  const int px = tx * P.tile_w + (int)threadIdx.x % P.tile_w;
-  const int py = ty * P.tile_h + (int)threadIdx.x / P.tile_w;
-  const bool inside = px < cam.W && py < cam.H;
-  const float x = (float)px + 0.5f, y = (float)py + 0.5f;
-  const int2 rg = ranges[cam.tile_base + tile];
-  const int lane = threadIdx.x & 31;
+  TileJob J;
+  J.x0 = (tile % cam.tiles_x) * P.tile_w;
+  J.y0 = (tile / cam.tiles_x) * P.tile_h;
+  J.W = cam.W;
+  J.H = cam.H;
+  J.rg = ranges[cam.tile_base + tile];
+  J.pix_base = 0;
+  fwd_tile<KID, PPT, COUNT>(rec, vals, P, J, smem, smem + B, smem + 2 * B, B, image, t_final, n_last, stats);
+}
 
-  float T = 1.f, Tf = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gT = 0.f;
-  int last = 0;
-  if (inside) {
-    const size_t p = (size_t)py * cam.W + px;
-    T = Tf = t_final[p];
-    last = n_last[p];
-    gC0 = grad_image[3 * p];
-    gC1 = grad_image[3 * p + 1];
-    gC2 = grad_image[3 * p + 2];
-    gT = grad_t ? grad_t[p] : 0.f;
+// ---------------------------------------------------------------- backward
+// Reduce-scatter of nine per-lane values over a warp.  Afterwards the warp
+// sum of value (lane >> 2) & 7 is in `mine` of every lane, and the sum of
+// v[8] in `ninth` of every lane.
+__device__ __forceinline__ void warp_reduce9(const float v[9], float& mine, float& ninth) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float w4[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = b4 ? v[i] : v[i + 4];
+    const float keep = b4 ? v[i + 4] : v[i];
+    w4[i] = keep + __shfl_xor_sync(FULL, send, 16);
   }
-  float S0 = P.bg[0] * Tf, S1 = P.bg[1] * Tf, S2 = P.bg[2] * Tf;
-  if (threadIdx.x == 0) s_max = 0;
+  float w2[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = b3 ? w4[i] : w4[i + 2];
+    const float keep = b3 ? w4[i + 2] : w4[i];
+    w2[i] = keep + __shfl_xor_sync(FULL, send, 8);
+  }
+  {
+    const float send = b2 ? w2[0] : w2[1];
+    const float keep = b2 ? w2[1] : w2[0];
+    mine = keep + __shfl_xor_sync(FULL, send, 4);
+  }
+  mine += __shfl_xor_sync(FULL, mine, 2);
+  mine += __shfl_xor_sync(FULL, mine, 1);
+  float u = v[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(FULL, u, o);
+  ninth = u;
+}
+
+template <int KID, int PPT>
+__device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
+                                         const ParDev& P, const TileJob& J, float4* s_a, float4* s_b, float4* s_c,
+                                         float* s_acc, uint32_t* s_id, int* s_touch, int* s_max, int B,
+                                         const float* __restrict__ t_final, const int32_t* __restrict__ n_last,
+                                         const float* __restrict__ grad_image, const float* __restrict__ grad_t,
+                                         float* __restrict__ g2d) {
+  const unsigned FULL = 0xffffffffu;
+  const int sx = P.tile_w / PPT;
+  const int lr = (int)threadIdx.x / sx, lc = ((int)threadIdx.x % sx) * PPT;
+  const int py = J.y0 + lr, px0 = J.x0 + lc;
+  const float y = (float)py + 0.5f;
+  const int lane = threadIdx.x & 31;
+  float xs[PPT], T[PPT], Tf[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gTv[PPT], S0[PPT], S1[PPT], S2[PPT];
+  int last[PPT];
+  int my_max = 0;
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    xs[p] = (float)(px0 + p) + 0.5f;
+    T[p] = Tf[p] = 1.f;
+    gC0[p] = gC1[p] = gC2[p] = gTv[p] = 0.f;
+    last[p] = 0;
+    if (px0 + p < J.W && py < J.H) {
+      const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p;
+      T[p] = Tf[p] = t_final[pi];
+      last[p] = n_last[pi];
+      gC0[p] = grad_image[3 * pi];
+      gC1[p] = grad_image[3 * pi + 1];
+      gC2[p] = grad_image[3 * pi + 2];
+      gTv[p] = grad_t ? grad_t[pi] : 0.f;
+    }
+    S0[p] = P.bg[0] * Tf[p];
+    S1[p] = P.bg[1] * Tf[p];
+    S2[p] = P.bg[2] * Tf[p];
+    my_max = max(my_max, last[p]);
+  }
+  if (threadIdx.x == 0) *s_max = 0;
   __syncthreads();
-  if (last > 0) atomicMax(&s_max, last);
+  if (my_max > 0) atomicMax(s_max, my_max);
   __syncthreads();
-  const int max_last = s_max;
+  const int max_last = *s_max;
 
   for (int b_end = max_last; b_end > 0; b_end -= B) {
     const int b0 = max(0, b_end - B);
     const int cnt = b_end - b0;
     __syncthreads();  // previous batch flushed
-    if ((int)threadIdx.x < cnt) {
-      const uint32_t id = vals[rg.x + b0 + threadIdx.x];
-      s_id[threadIdx.x] = id;
-      s_a[threadIdx.x] = rec[3 * (size_t)id];
-      s_b[threadIdx.x] = rec[3 * (size_t)id + 1];
-      s_c[threadIdx.x] = rec[3 * (size_t)id + 2];
-      s_touch[threadIdx.x] = 0;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      const uint32_t id = vals[J.rg.x + b0 + k];
+      s_id[k] = id;
+      s_a[k] = rec[3 * (size_t)id];
+      s_b[k] = rec[3 * (size_t)id + 1];
+      s_c[k] = rec[3 * (size_t)id + 2];
+      s_touch[k] = 0;
 #pragma unroll
-      for (int m = 0; m < 9; ++m) s_acc[9 * threadIdx.x + m] = 0.f;
+      for (int m = 0; m < 9; ++m) s_acc[9 * k + m] = 0.f;
     }
     __syncthreads();
     for (int jj = cnt - 1; jj >= 0; --jj) {
       const int j = b0 + jj;
+      const float4 a = s_a[jj];
+      const float4 bb = s_b[jj];
+      const float dy = __fsub_rn(y, a.y);
+      const float l01dy = __fmul_rn(a.w, dy);
+      const float e2 = __fmul_rn(bb.x, dy);
+      const float e2s = __fmul_rn(e2, e2);
       float v[9];
 #pragma unroll
       for (int m = 0; m < 9; ++m) v[m] = 0.f;
-      bool contrib = false;
-      if (j < last) {
-        const float4 a = s_a[jj];
-        const float4 bb = s_b[jj];
-        PairEval e;
-        if (pair_alpha<KID>(x, y, a, bb, P, e)) {
-          const float dx = e.dx, dy = e.dy, D = e.D, xk = e.xk, f = e.f, araw = e.araw, alpha = e.alpha;
-          {
-            contrib = true;
-            const float4 c = s_c[jj];
-            const float om = 1.f - alpha;
-            const float iom = 1.f / om;
-            const float Tb = T * iom;  // transmittance in front of this entry
-            const float wgt = alpha * Tb;
-            v[6] = wgt * gC0;
-            v[7] = wgt * gC1;
-            v[8] = wgt * gC2;
-            const float ga = gC0 * (c.x * Tb - S0 * iom) + gC1 * (c.y * Tb - S1 * iom) +
-                             gC2 * (c.z * Tb - S2 * iom) - gT * Tf * iom;
-            S0 += c.x * wgt;
-            S1 += c.y * wgt;
-            S2 += c.z * wgt;
-            T = Tb;
-            if (araw <= P.alpha_max) {
-              v[5] = f * ga;
-              float gD = bb.y * ga * kern_df<KID>(xk) * P.inv_lambda;
-              if (P.ags == 1) gD *= __expf(-D * D);
-              else if (P.ags == 2) gD *= __expf(-xk * xk);
-              const float gq = D > 0.f ? 0.5f * gD / D : 0.f;
-              // A d = L^T (L d)
-              v[0] = -2.f * gq * (a.z * e.e1);
-              v[1] = -2.f * gq * (a.w * e.e1 + bb.x * e.e2);
-              v[2] = gq * dx * dx;
-              v[3] = 2.f * gq * dx * dy;
-              v[4] = gq * dy * dy;
-            }
-          }
+      bool any = false;
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) {
+        float dx, e1;
+        const float q = pair_q(xs[p], a.x, a.z, l01dy, e2s, dx, e1);
+        if (j >= last[p] || q > bb.z) continue;
+        float D, xk, f, araw, alpha;
+        pair_alpha<KID>(q, bb.y, P, D, xk, f, araw, alpha);
+        if (alpha < P.alpha_min) continue;
+        any = true;
+        const float4 c = s_c[jj];
+        const float iom = 1.f / (1.f - alpha);
+        const float Tb = T[p] * iom;  // transmittance in front of this entry
+        const float wgt = alpha * Tb;
+        v[6] += wgt * gC0[p];
+        v[7] += wgt * gC1[p];
+        v[8] += wgt * gC2[p];
+        const float ga = gC0[p] * (c.x * Tb - S0[p] * iom) + gC1[p] * (c.y * Tb - S1[p] * iom) +
+                         gC2[p] * (c.z * Tb - S2[p] * iom) - gTv[p] * Tf[p] * iom;
+        S0[p] += c.x * wgt;
+        S1[p] += c.y * wgt;
+        S2[p] += c.z * wgt;
+        T[p] = Tb;
+        if (araw <= P.alpha_max) {
+          v[5] += f * ga;
+          float gD = bb.y * ga * kern_df<KID>(xk) * P.inv_lambda;
+          if (P.ags == 1) gD *= __expf(-D * D);
+          else if (P.ags == 2) gD *= __expf(-xk * xk);
+          const float gq = D > 0.f ? 0.5f * gD / D : 0.f;
+          // A d = L^T (L d) = (l00 e1, l01 e1 + l11 e2)
+          v[0] += -2.f * gq * (a.z * e1);
+          v[1] += -2.f * gq * (a.w * e1 + bb.x * e2);
+          v[2] += gq * dx * dx;
+          v[3] += 2.f * gq * dx * dy;
+          v[4] += gq * dy * dy;
         }
       }
-      if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-          for (int m = 0; m < 9; ++m) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
-        if (lane == 0) {
+      const unsigned bal = __ballot_sync(FULL, any);
+      if (bal == 0u) continue;
+      if (__popc(bal) == 1) {
+        if (any) {
 #pragma unroll
           for (int m = 0; m < 9; ++m) atomicAdd(&s_acc[9 * jj + m], v[m]);
+          s_touch[jj] = 1;
+        }
+      } else {
+        float mine, ninth;
+        warp_reduce9(v, mine, ninth);
+        if ((lane & 3) == 0) atomicAdd(&s_acc[9 * jj + (lane >> 2)], mine);
+        if (lane == 1) {
+          atomicAdd(&s_acc[9 * jj + 8], ninth);
           s_touch[jj] = 1;
         }
       }
     }
     __syncthreads();
-    if ((int)threadIdx.x < cnt && s_touch[threadIdx.x]) {
-      const float* acc = s_acc + 9 * threadIdx.x;
-      float* dst = g2d + 12 * (size_t)s_id[threadIdx.x];
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      if (!s_touch[k]) continue;
+      const float* acc = s_acc + 9 * k;
+      float* dst = g2d + 12 * (size_t)s_id[k];
       atomicAdd(reinterpret_cast<float4*>(dst), make_float4(acc[0], acc[1], acc[2], acc[3]));
       atomicAdd(reinterpret_cast<float4*>(dst + 4), make_float4(acc[4], acc[5], acc[6], acc[7]));
       atomicAdd(dst + 8, acc[8]);
@@ -271,21 +360,55 @@ __global__ void __launch_bounds__(512) blend_bwd_kernel(const float4* __restrict
   }
 }
 
+template <int KID, int PPT>
+__global__ void __launch_bounds__(128) blend_bwd_kernel(const float4* __restrict__ rec, const CamDev cam,
+                                                        const ParDev P, const int2* __restrict__ ranges,
+                                                        const uint32_t* __restrict__ vals,
+                                                        const float* __restrict__ t_final,
+                                                        const int32_t* __restrict__ n_last,
+                                                        const float* __restrict__ grad_image,
+                                                        const float* __restrict__ grad_t, float* __restrict__ g2d) {
+  extern __shared__ float4 smem[];
+  __shared__ int s_max;
+  const int B = 2 * blockDim.x;
+  float* s_acc = reinterpret_cast<float*>(smem + 3 * B);
+  uint32_t* s_id = reinterpret_cast<uint32_t*>(s_acc + 9 * B);
+  int* s_touch = reinterpret_cast<int*>(s_id + B);
+  const int tile = blockIdx.x;
+  TileJob J;
+  J.x0 = (tile % cam.tiles_x) * P.tile_w;
+  J.y0 = (tile / cam.tiles_x) * P.tile_h;
+  J.W = cam.W;
+  J.H = cam.H;
+  J.rg = ranges[cam.tile_base + tile];
+  J.pix_base = 0;
+  bwd_tile<KID, PPT>(rec, vals, P, J, smem, smem + B, smem + 2 * B, s_acc, s_id, s_touch, &s_max, B, t_final, n_last,
+                     grad_image, grad_t, g2d);
+}
+
 }  // namespace
+
+// Pixels per thread: 4 for tiles of 256+ pixels, 2 for 8x8 (one warp).
+static inline int ppt_for(const ParDev& P) { return P.tile_w * P.tile_h >= 256 ? 4 : 2; }
 
 cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
                              const uint32_t* vals, float* image, float* t_final, int32_t* n_last,
                              unsigned long long* stats, cudaStream_t st) {
-  const int B = P.tile_w * P.tile_h;
+  const int ppt = ppt_for(P);
+  const int threads = P.tile_w * P.tile_h / ppt;
   const unsigned grid = (unsigned)(cam.tiles_x * cam.tiles_y);
-  const size_t sm = sizeof(float4) * 3 * B;
-#define LS_BF(K)                                                                                           \
-  do {                                                                                                     \
-    if (stats)                                                                                             \
-      blend_fwd_kernel<K, true><<<grid, B, sm, st>>>(rec, cam, P, ranges, vals, image, t_final, n_last, stats); \
-    else                                                                                                   \
-      blend_fwd_kernel<K, false><<<grid, B, sm, st>>>(rec, cam, P, ranges, vals, image, t_final, n_last,     \
-                                                      nullptr);                                            \
+  const size_t sm = sizeof(float4) * 3 * 4 * threads;
+#define LS_BF3(K, PP, C) \
+  blend_fwd_kernel<K, PP, C><<<grid, threads, sm, st>>>(rec, cam, P, ranges, vals, image, t_final, n_last, stats)
+#define LS_BF2(K, PP)               \
+  do {                              \
+    if (stats) LS_BF3(K, PP, true); \
+    else LS_BF3(K, PP, false);      \
+  } while (0)
+#define LS_BF(K)                \
+  do {                          \
+    if (ppt == 4) LS_BF2(K, 4); \
+    else LS_BF2(K, 2);          \
   } while (0)
   switch (P.kernel) {
     case LS_KERNEL_GAUSSIAN: LS_BF(LS_KERNEL_GAUSSIAN); break;
@@ -295,18 +418,27 @@ cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev&
     default: LS_BF(LS_KERNEL_LINEAR); break;
   }
 #undef LS_BF
+#undef LS_BF2
+#undef LS_BF3
   return cudaGetLastError();
 }
 
 cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
                              const uint32_t* vals, const float* t_final, const int32_t* n_last,
                              const float* grad_image, const float* grad_t, float* g2d, cudaStream_t st) {
-  const int B = P.tile_w * P.tile_h;
+  const int ppt = ppt_for(P);
+  const int threads = P.tile_w * P.tile_h / ppt;
+  const int B = 2 * threads;
   const unsigned grid = (unsigned)(cam.tiles_x * cam.tiles_y);
   const size_t sm = sizeof(float4) * 3 * B + sizeof(float) * 9 * B + 2 * sizeof(uint32_t) * B;
-#define LS_BB(K)                                                                                        \
-  blend_bwd_kernel<K><<<grid, B, sm, st>>>(rec, cam, P, ranges, vals, t_final, n_last, grad_image, grad_t, \
-                                           g2d)
+#define LS_BB2(K, PP)                                                                                          \
+  blend_bwd_kernel<K, PP><<<grid, threads, sm, st>>>(rec, cam, P, ranges, vals, t_final, n_last, grad_image, \
+                                                     grad_t, g2d)
+#define LS_BB(K)                \
+  do {                          \
+    if (ppt == 4) LS_BB2(K, 4); \
+    else LS_BB2(K, 2);          \
+  } while (0)
   switch (P.kernel) {
     case LS_KERNEL_GAUSSIAN: LS_BB(LS_KERNEL_GAUSSIAN); break;
     case LS_KERNEL_LAPLACIAN: LS_BB(LS_KERNEL_LAPLACIAN); break;
@@ -315,6 +447,7 @@ cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev&
     default: LS_BB(LS_KERNEL_LINEAR); break;
   }
 #undef LS_BB
+#undef LS_BB2
   return cudaGetLastError();
 }
 
