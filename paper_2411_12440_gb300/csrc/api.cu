@@ -224,10 +224,10 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
   if (R > 0) {
     LS_TRY(launch_radix_hist(pp.dkey, nullptr, R, 0, 4, ds.hist, st));
     LS_TRY(launch_radix_scan(ds.hist, 4, st));
-    LS_TRY(launch_onesweep_pass(pp.dkey, nullptr, w.dk_b, w.dv_b, nullptr, R, R, 0, 0, ds, status_dev, st));
-    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 1, ds, status_dev, st));
-    LS_TRY(launch_onesweep_pass(w.dk_a, w.dv_a, w.dk_b, w.dv_b, nullptr, R, R, 0, 2, ds, status_dev, st));
-    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 3, ds, status_dev, st));
+    LS_TRY(launch_onesweep_pass(pp.dkey, nullptr, w.dk_b, w.dv_b, nullptr, R, R, 0, 0, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 1, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_a, w.dv_a, w.dk_b, w.dv_b, nullptr, R, R, 0, 2, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 3, ds, nullptr, status_dev, st));
     LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n_per_cam, P, w.rect, w.block_sums, st));
   }
   LS_TRY(launch_dup_scan(R, w.block_sums, key_capacity, n_keys_dev, w.n_valid, status_dev, st));
@@ -238,16 +238,19 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
   uint32_t* ok = (kp % 2 == 0) ? w.k_alt : keys;
   uint32_t* ov = (kp % 2 == 0) ? w.v_alt : vals;
   SortScratch ts = sort_scratch_carve(w.tile_scratch, key_capacity > 0 ? key_capacity : 1, kp);
+  // ranges: accumulated by the last tile pass as (min start, ~max end)
+  LS_TRY(cudaMemsetAsync(tile_ranges, 0xFF, sizeof(int32_t) * 2 * (size_t)total_tiles, st));
   if (R > 0 && key_capacity > 0) {
     LS_TRY(launch_dup_emit(R, w.dv_a, w.rect, w.block_sums, T, n_per_cam, w.n_valid, ek, ev, kp, ts.hist, st));
     LS_TRY(launch_radix_scan(ts.hist, kp, st));
     for (int p = 0; p < kp; ++p) {
-      LS_TRY(launch_onesweep_pass(ek, ev, ok, ov, w.n_valid, 0, key_capacity, 0, p, ts, status_dev, st));
+      LS_TRY(launch_onesweep_pass(ek, ev, ok, ov, w.n_valid, 0, key_capacity, 0, p, ts,
+                                  p == kp - 1 ? tile_ranges : nullptr, status_dev, st));
       std::swap(ek, ok);
       std::swap(ev, ov);
     }
   }
-  LS_TRY(launch_tile_ranges(keys, w.n_valid, key_capacity, tile_ranges, (int)total_tiles, st));
+  LS_TRY(launch_ranges_fixup(tile_ranges, (int)total_tiles, st));
   return LS_OK;
 }
 

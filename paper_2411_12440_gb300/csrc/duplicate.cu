@@ -203,16 +203,6 @@ __global__ void __launch_bounds__(DUP_THREADS) dup_emit_kernel(int64_t R, const 
   }
 }
 
-__global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __restrict__ keys, const int64_t* n_valid,
-                                                          int2* __restrict__ ranges) {
-  const int64_t n = *n_valid;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t t = keys[k];
-    if (k == 0 || keys[k - 1] != t) ranges[t].x = (int)k;
-    if (k == n - 1 || keys[k + 1] != t) ranges[t].y = (int)(k + 1);
-  }
-}
-
 }  // namespace
 
 cudaError_t launch_dup_count(int64_t R, const uint32_t* order, const uint32_t* dkey_sorted, const float4* foot,
@@ -237,17 +227,6 @@ cudaError_t launch_dup_emit(int64_t R, const uint32_t* order, const uint2* rect_
   if (R == 0) return cudaSuccess;
   dup_emit_kernel<<<ceil_div(R, DUP_BLOCK), DUP_THREADS, 0, st>>>(R, order, rect_sorted, block_offs, cams, n_per_cam,
                                                                  n_valid_dev, keys, vals, key_passes, tile_hist);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_tile_ranges(const uint32_t* keys, const int64_t* n_valid_dev, int64_t cap, int32_t* ranges,
-                               int total_tiles, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)total_tiles, st);
-  if (e != cudaSuccess) return e;
-  int64_t want = cap > 0 ? cap : 1;
-  unsigned grid = ceil_div(want, 256);
-  if (grid > 152u * 16u) grid = 152u * 16u;
-  tile_ranges_kernel<<<grid, 256, 0, st>>>(keys, n_valid_dev, reinterpret_cast<int2*>(ranges));
   return cudaGetLastError();
 }
 

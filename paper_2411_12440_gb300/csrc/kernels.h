@@ -41,10 +41,14 @@ cudaError_t launch_radix_scan(uint32_t* hist, int passes, cudaStream_t st);
 // One onesweep pass (digit `pass`, bits [begin_bit + 8 pass, +8)).
 // vals_in == nullptr means the identity values 0..n-1.  n is read from
 // n_dev when not null, else n_host; the grid covers `cap` keys.
+// ranges != nullptr on the last pass of a tile sort: the pass also records
+// each tile's [start, end) (prefilled with 0xFF bytes, finished by
+// launch_ranges_fixup).
 cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                                  uint32_t* vals_out, const int64_t* n_dev, int64_t n_host, int64_t cap,
-                                 int begin_bit, int pass, const SortScratch& s, int32_t* status,
+                                 int begin_bit, int pass, const SortScratch& s, int32_t* ranges, int32_t* status,
                                  cudaStream_t st);
+cudaError_t launch_ranges_fixup(int32_t* ranges, int total_tiles, cudaStream_t st);
 
 // ---- duplication and tile ranges (duplicate.cu)
 constexpr int DUP_THREADS = 256;
@@ -58,8 +62,6 @@ cudaError_t launch_dup_scan(int64_t R, uint32_t* block_sums, int64_t cap, int64_
 cudaError_t launch_dup_emit(int64_t R, const uint32_t* order, const uint2* rect_sorted, const uint32_t* block_offs,
                             const CamTable& cams, int n_per_cam, const int64_t* n_valid_dev, uint32_t* keys,
                             uint32_t* vals, int key_passes, uint32_t* tile_hist, cudaStream_t st);
-cudaError_t launch_tile_ranges(const uint32_t* keys, const int64_t* n_valid_dev, int64_t cap, int32_t* ranges,
-                               int total_tiles, cudaStream_t st);
 
 // ---- blending (blend.cu)
 cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,

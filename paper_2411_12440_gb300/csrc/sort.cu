@@ -81,42 +81,64 @@ __global__ void __launch_bounds__(RADIX) radix_scan_kernel(uint32_t* hist) {
   h[threadIdx.x] = incl - v;
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) onesweep_kernel(
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Dynamic shared memory of one onesweep block.
+struct OnesweepSmem {
+  uint32_t keys[SORT_PART];      // keys in block-sorted order
+  uint32_t vin[SORT_PART];       // the partition's values in input order (cp.async)
+  uint16_t src[SORT_PART];       // input position of the key at each sorted slot
+  uint32_t whist[SORT_WARPS][RADIX];
+  uint32_t local[RADIX];
+  uint32_t glob[RADIX];
+  uint32_t warp[SORT_WARPS];
+  uint32_t part;
+};
+
+__global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const int64_t* n_dev, int64_t n_host, int shift,
-    const uint32_t* __restrict__ digit_base, uint64_t* lookback, uint32_t* part_ctr, int32_t* status) {
-  __shared__ uint32_t s_keys[SORT_PART];
-  __shared__ uint32_t s_vals[SORT_PART];
-  __shared__ uint32_t s_whist[SORT_WARPS][RADIX];
-  __shared__ uint32_t s_local[RADIX];
-  __shared__ uint32_t s_glob[RADIX];
-  __shared__ uint32_t s_warp[SORT_WARPS];
-  __shared__ uint32_t s_part;
+    const uint32_t* __restrict__ digit_base, uint64_t* lookback, uint32_t* part_ctr, uint2* ranges,
+    int32_t* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  OnesweepSmem& S = *reinterpret_cast<OnesweepSmem*>(smem_raw);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&s_whist[0][0])[i] = 0;
-  if (tid == 0) s_part = atomicAdd(part_ctr, 1u);
+  for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&S.whist[0][0])[i] = 0;
+  if (tid == 0) S.part = atomicAdd(part_ctr, 1u);
   __syncthreads();
   const int64_t n = n_dev ? *n_dev : n_host;
-  const uint32_t part = s_part;
+  const uint32_t part = S.part;
   const int64_t base = (int64_t)part * SORT_PART;
   if (base >= n) return;  // block-uniform
+  const int n_in = (int)(n - base < SORT_PART ? n - base : SORT_PART);
 
-  // warp-striped load: warp w holds positions base + w*32*ITEMS + i*32 + lane
-  const int64_t wbase = base + (int64_t)warp * 32 * SORT_ITEMS;
+  // values: asynchronous copy into shared memory, in flight during ranking
+  if (vals_in) {
+    for (int i = tid; i < n_in; i += SORT_THREADS) cp_async4(&S.vin[i], vals_in + base + i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  // keys: warp-striped, warp w holds positions w*32*ITEMS + i*32 + lane
+  const int wofs = warp * 32 * SORT_ITEMS;
   uint32_t k[SORT_ITEMS];
-  uint32_t rank[SORT_ITEMS];
 #pragma unroll
   for (int i = 0; i < SORT_ITEMS; ++i) {
-    int64_t idx = wbase + i * 32 + lane;
-    k[i] = idx < n ? keys_in[idx] : 0xFFFFFFFFu;
+    const int li = wofs + i * 32 + lane;
+    k[i] = li < n_in ? keys_in[base + li] : 0xFFFFFFFFu;
   }
   // rank inside the warp: peers with the same digit from 8 ballots; items are
-  // visited in position order, so ranks are stable
+  // visited in position order, so ranks are stable.  Ranks fit 16 bits.
+  uint32_t rk[(SORT_ITEMS + 1) / 2];
+#pragma unroll
+  for (int i = 0; i < (SORT_ITEMS + 1) / 2; ++i) rk[i] = 0;
   const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
   for (int i = 0; i < SORT_ITEMS; ++i) {
-    const bool valid = wbase + i * 32 + lane < n;
+    const bool valid = wofs + i * 32 + lane < n_in;
     const uint32_t d = (k[i] >> shift) & 255u;
     uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
@@ -125,10 +147,10 @@ __global__ void __launch_bounds__(SORT_THREADS) onesweep_kernel(
       const uint32_t bal = __ballot_sync(0xffffffffu, bit);
       peers &= bit ? bal : ~bal;
     }
-    const uint32_t before = s_whist[warp][d];
+    const uint32_t before = S.whist[warp][d];
     __syncwarp();
-    rank[i] = before + __popc(peers & lt);
-    if (valid && lane == 31 - __clz(peers)) s_whist[warp][d] = before + __popc(peers);
+    rk[i / 2] |= (before + __popc(peers & lt)) << (16 * (i & 1));
+    if (valid && lane == 31 - __clz(peers)) S.whist[warp][d] = before + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
@@ -139,14 +161,14 @@ __global__ void __launch_bounds__(SORT_THREADS) onesweep_kernel(
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < SORT_WARPS; ++w) {
-      uint32_t c = s_whist[w][d];
-      s_whist[w][d] = run;
+      uint32_t c = S.whist[w][d];
+      S.whist[w][d] = run;
       run += c;
     }
     uint64_t* my = lookback + (size_t)part * RADIX + d;
     st_relaxed_u64(my, (part == 0 ? LB_INC : LB_AGG) | (uint64_t)run);
-    const uint32_t incl = block_incl_scan(run, s_warp);
-    s_local[d] = incl - run;
+    const uint32_t incl = block_incl_scan(run, S.warp);
+    S.local[d] = incl - run;
     uint64_t prefix = 0;
     if (part > 0) {
       int64_t p = (int64_t)part - 1;
@@ -166,32 +188,47 @@ __global__ void __launch_bounds__(SORT_THREADS) onesweep_kernel(
       }
       st_relaxed_u64(my, LB_INC | (prefix + run));
     }
-    s_glob[d] = digit_base[d] + (uint32_t)prefix - s_local[d];
+    S.glob[d] = digit_base[d] + (uint32_t)prefix - S.local[d];
   }
   __syncthreads();
 
-  // stage in block-sorted order
+  // stage the keys (and where each came from) in block-sorted order
 #pragma unroll
   for (int i = 0; i < SORT_ITEMS; ++i) {
-    const int64_t idx = wbase + i * 32 + lane;
-    if (idx < n) {
+    const int li = wofs + i * 32 + lane;
+    if (li < n_in) {
       const uint32_t d = (k[i] >> shift) & 255u;
-      const uint32_t pos = s_local[d] + s_whist[warp][d] + rank[i];
-      s_keys[pos] = k[i];
-      s_vals[pos] = vals_in ? vals_in[idx] : (uint32_t)idx;
+      const uint32_t pos = S.local[d] + S.whist[warp][d] + ((rk[i / 2] >> (16 * (i & 1))) & 0xFFFFu);
+      S.keys[pos] = k[i];
+      S.src[pos] = (uint16_t)li;
     }
   }
+  if (vals_in) cp_async_wait_all();
   __syncthreads();
   // digit runs go to consecutive global positions
-  const int n_in = (int)(n - base < SORT_PART ? n - base : SORT_PART);
   for (int s = tid; s < n_in; s += SORT_THREADS) {
-    const uint32_t key = s_keys[s];
-    const uint32_t dst = s_glob[(key >> shift) & 255u] + (uint32_t)s;
+    const uint32_t key = S.keys[s];
+    const uint32_t dst = S.glob[(key >> shift) & 255u] + (uint32_t)s;
     if (dst < (uint64_t)n) {
       keys_out[dst] = key;
-      vals_out[dst] = s_vals[s];
+      vals_out[dst] = vals_in ? S.vin[S.src[s]] : (uint32_t)(base + S.src[s]);
+      if (ranges) {
+        // last pass of a tile sort: the block's keys are fully sorted, so a
+        // tile's entries here form one run; record its ends
+        if (s == 0 || S.keys[s - 1] != key) atomicMin(&ranges[key].x, dst);
+        if (s == n_in - 1 || S.keys[s + 1] != key) atomicMin(&ranges[key].y, ~(dst + 1u));
+      }
     }
   }
+}
+
+// Ranges were accumulated as (min start, ~max end) from 0xFFFFFFFF; empty
+// tiles become [0, 0).
+__global__ void __launch_bounds__(256) ranges_fixup_kernel(uint2* ranges, int total_tiles) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total_tiles) return;
+  uint2 r = ranges[t];
+  ranges[t] = (r.x == 0xFFFFFFFFu) ? make_uint2(0u, 0u) : make_uint2(r.x, ~r.y);
 }
 
 inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -230,13 +267,29 @@ cudaError_t launch_radix_scan(uint32_t* hist, int passes, cudaStream_t st) {
 
 cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                                  uint32_t* vals_out, const int64_t* n_dev, int64_t n_host, int64_t cap,
-                                 int begin_bit, int pass, const SortScratch& s, int32_t* status,
+                                 int begin_bit, int pass, const SortScratch& s, int32_t* ranges, int32_t* status,
                                  cudaStream_t st) {
+  // the dynamic shared memory limit is a per-device attribute of the kernel
+  static bool attr_set[64] = {false};
+  const size_t sm = sizeof(OnesweepSmem);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
   unsigned grid = ceil_div(cap > 0 ? cap : 1, SORT_PART);
-  onesweep_kernel<<<grid, SORT_THREADS, 0, st>>>(keys_in, vals_in, keys_out, vals_out, n_dev, n_host,
-                                                 begin_bit + 8 * pass, s.hist + (size_t)pass * RADIX,
-                                                 s.lookback + (size_t)pass * s.parts * RADIX, s.part_ctr + pass,
-                                                 status);
+  onesweep_kernel<<<grid, SORT_THREADS, sm, st>>>(keys_in, vals_in, keys_out, vals_out, n_dev, n_host,
+                                                  begin_bit + 8 * pass, s.hist + (size_t)pass * RADIX,
+                                                  s.lookback + (size_t)pass * s.parts * RADIX, s.part_ctr + pass,
+                                                  reinterpret_cast<uint2*>(ranges), status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ranges_fixup(int32_t* ranges, int total_tiles, cudaStream_t st) {
+  ranges_fixup_kernel<<<ceil_div(total_tiles, 256), 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
   return cudaGetLastError();
 }
 
