@@ -207,6 +207,57 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+# batched form: 64 cameras of uneven resolution, one graph-captured launch
+# --------------------------------------------------------------------------
+def bench_batched(dev, reps=10):
+    import dataclasses
+    import torch
+    from paper_2411_12440_gb300 import raster, scenes
+    from paper_2411_12440_gb300.batch import Autotuner, BatchRenderer
+    scene, cams, extra = scenes.make_workload("batch_3m_64cams")
+    sp = raster.Splats.from_scene(scene, device=dev)
+    P = raster.RenderParams(sh_degree=3)
+    tune = Autotuner(reps=2).tune(sp, cams, P, device=dev)
+    Pt = dataclasses.replace(P, tile_w=tune.tile[0], tile_h=tune.tile[1])
+    br = BatchRenderer(sp, cams, Pt, blend_batch=tune.blend_batch, device=dev)
+    br.plan()
+    br.capture()
+    for _ in range(2):
+        br.render()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        br.render()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    br.check()
+    ms_batch = e0.elapsed_time(e1) / reps
+    K = int(br.n_keys.item())
+    del br
+    torch.cuda.empty_cache()
+    # the plain path, one camera at a time, same tile shape
+    rz = raster.Rasterizer(dataclasses.replace(Pt), device=dev)
+    for cam in cams:
+        rz.forward(sp, cam, sync_capacity=True)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for cam in cams:
+        rz.forward(sp, cam, sync_capacity=False)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    rz.check_status("plain cameras")
+    ms_plain = e0.elapsed_time(e1)
+    pixels = sum(c["width"] * c["height"] for c in cams)
+    return {"workload": "batch_3m_64cams", "cams": len(cams), "prims": scene.n, "pixels": pixels, "tile_keys": K,
+            "tile": "%dx%d" % tune.tile, "blend_batch": tune.blend_batch, "graph": True,
+            "ms_per_batch": ms_batch, "frames_per_s": len(cams) * 1e3 / ms_batch,
+            "plain_ms_per_batch": ms_plain, "plain_frames_per_s": len(cams) * 1e3 / ms_plain,
+            "speedup_vs_plain": ms_plain / ms_batch,
+            "autotune_ms": {"%dx%d/b%d" % k: round(v, 3) for k, v in tune.table.items()}}
+
+
+# --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
 def main():
@@ -219,6 +270,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-camera batched measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -403,6 +455,8 @@ def main():
             # scan, kp tile passes, ranges); blend fwd, blend bwd, project bwd 1 each
             "gpu_launches": args.steps * (1 + (11 + kp) + 3)}
 
+    if not args.no_batch and args.prims is None:
+        line["batched"] = bench_batched(dev)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         ncores = os.cpu_count() or 1
         est, sample, spent = oracle_frame_estimate(scene, cam, dict(sh_degree=3, antialias=int(extra["antialias"])),

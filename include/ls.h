@@ -187,6 +187,29 @@ ls_status ls_render_bwd(int32_t n, const float* means, const float* scales, cons
                         float* g_sh, float* g2d_out, void* workspace, size_t ws_bytes, int32_t* status_dev,
                         void* stream);
 
+/* Workspace of ls_render_batch in bytes (projected records, keys, ranges,
+ * job queue and the duplicate/sort scratch). */
+size_t ls_render_batch_workspace(int32_t n, const ls_camera* cams, int32_t n_cams, const ls_params* params,
+                                 int64_t key_capacity);
+
+/* a7: forward render of n_cams cameras (1..LS_MAX_CAMS, sizes may differ)
+ * in one pass: projection of all (camera, primitive) records, one shared
+ * duplicate/sort over global tile ids, a queue of every (camera, tile) job
+ * with the longest lists first, and one persistent blending launch whose
+ * CTAs take jobs until the queue is empty.  Per pixel the result is exactly
+ * ls_render_fwd's for that camera.  Parameters as ls_project; blend_batch =
+ * records staged per shared-memory batch (16..1024, 0 = default).  Outputs:
+ * images [sum_c H_c W_c][3] float, camera c's image starting at pixel
+ * sum_{c'<c} H_c' W_c'; t_final (same pixel layout) or NULL; *n_keys_dev = K.
+ * key_capacity and LS_ERR_CAPACITY as for ls_duplicate_sort.  Nothing in the
+ * call synchronises with the host, so a caller can capture it in a CUDA graph
+ * once the dynamic-shared-memory attributes are set (any earlier call). */
+ls_status ls_render_batch(int32_t n, const float* means, const float* scales, const float* quats,
+                          const float* opacities, const float* sh, const ls_camera* cams, int32_t n_cams,
+                          const ls_params* params, int32_t blend_batch, int64_t key_capacity, float* images,
+                          float* t_final, int64_t* n_keys_dev, void* workspace, size_t ws_bytes,
+                          int32_t* status_dev, void* stream);
+
 /* ls_duplicate_sort without a caller-supplied workspace, for callers that
  * cannot allocate device memory themselves: a plugin running inside a host
  * application that owns every device allocation, a real-time loop that must

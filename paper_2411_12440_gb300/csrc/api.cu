@@ -349,4 +349,87 @@ ls_status ls_render_bwd(int32_t n, const float* means, const float* scales, cons
   return LS_OK;
 }
 
+// ---------------------------------------------------------------- batched render
+namespace {
+
+struct BatchWs {
+  char* proj;
+  uint32_t *keys, *vals;
+  int32_t* ranges;
+  uint32_t* queue;
+  unsigned* job_ctr;
+  char* dup;
+  size_t dup_bytes, total;
+};
+
+BatchWs batch_layout(char* base, int64_t R, int64_t cap, int64_t total_tiles) {
+  BatchWs w;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base + off;
+    off += al256(bytes);
+    return p;
+  };
+  const size_t Cz = (size_t)(cap > 0 ? cap : 1);
+  w.proj = take(ls_proj_bytes(R > 0 ? R : 1));
+  w.keys = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.vals = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.ranges = reinterpret_cast<int32_t*>(take(8 * (size_t)total_tiles));
+  w.queue = reinterpret_cast<uint32_t*>(take(4 * (size_t)total_tiles));
+  w.job_ctr = reinterpret_cast<unsigned*>(take(4));
+  w.dup_bytes = ls_duplicate_sort_workspace(R, cap, (int32_t)total_tiles);
+  w.dup = take(w.dup_bytes);
+  w.total = off;
+  return w;
+}
+
+}  // namespace
+
+size_t ls_render_batch_workspace(int32_t n, const ls_camera* cams, int32_t n_cams, const ls_params* params,
+                                 int64_t key_capacity) {
+  if (n < 0 || key_capacity < 0 || !params_ok(params)) return 0;
+  CamTable T;
+  int64_t total_tiles = 0;
+  if (!make_cams(cams, n_cams, params, T, &total_tiles)) return 0;
+  return batch_layout(nullptr, (int64_t)n * n_cams, key_capacity, total_tiles).total;
+}
+
+ls_status ls_render_batch(int32_t n, const float* means, const float* scales, const float* quats,
+                          const float* opacities, const float* sh, const ls_camera* cams, int32_t n_cams,
+                          const ls_params* params, int32_t blend_batch, int64_t key_capacity, float* images,
+                          float* t_final, int64_t* n_keys_dev, void* workspace, size_t ws_bytes,
+                          int32_t* status_dev, void* stream) {
+  if (n < 0 || !params_ok(params)) return LS_ERR_INVALID_ARG;
+  if (blend_batch != 0 && (blend_batch < 16 || blend_batch > 1024)) return LS_ERR_INVALID_ARG;
+  CamTable T;
+  int64_t total_tiles = 0;
+  if (!make_cams(cams, n_cams, params, T, &total_tiles)) return LS_ERR_INVALID_ARG;
+  const int64_t R = (int64_t)n * n_cams;
+  if (R > 0x7FFFFFFFll || key_capacity < 0 || key_capacity > 0x7FFFFFFFll) return LS_ERR_INVALID_ARG;
+  if (!images || !n_keys_dev || !workspace) return LS_ERR_INVALID_ARG;
+  if (n > 0 && (!means || !scales || !quats || !opacities || !sh)) return LS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(quats) % 16 || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return LS_ERR_INVALID_ARG;
+  BatchWs w = batch_layout(static_cast<char*>(workspace), R, key_capacity, total_tiles);
+  if (ws_bytes < w.total) return LS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ParDev P = make_par(params);
+  BatchPix pix;
+  size_t acc = 0;
+  for (int c = 0; c < n_cams; ++c) {
+    pix.base[c] = acc;
+    acc += (size_t)cams[c].width * cams[c].height;
+  }
+  if (n > 0) {
+    LS_TRY(launch_project_fwd(n, means, scales, quats, opacities, sh, T, P, proj_planes(w.proj, R), nullptr, st));
+  }
+  ls_status s = ls_duplicate_sort(R, w.proj, cams, n_cams, params, key_capacity, w.keys, w.vals, n_keys_dev,
+                                  w.ranges, w.dup, w.dup_bytes, status_dev, stream);
+  if (s != LS_OK) return s;
+  LS_TRY(launch_build_queue(w.ranges, (int)total_tiles, w.queue, w.job_ctr, st));
+  LS_TRY(launch_blend_batch(proj_cplanes(w.proj, R).rec, w.vals, w.ranges, T, pix, P, w.queue, (int)total_tiles,
+                            w.job_ctr, images, t_final, blend_batch, st));
+  return LS_OK;
+}
+
 }  // extern "C"

@@ -137,8 +137,8 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
       image[3 * pi] = C0[p] + T[p] * P.bg[0];
       image[3 * pi + 1] = C1[p] + T[p] * P.bg[1];
       image[3 * pi + 2] = C2[p] + T[p] * P.bg[2];
-      t_final[pi] = T[p];
-      n_last[pi] = last[p];
+      if (t_final) t_final[pi] = T[p];
+      if (n_last) n_last[pi] = last[p];
     }
   }
   if (COUNT) {
@@ -386,6 +386,77 @@ __global__ void __launch_bounds__(128) blend_bwd_kernel(const float4* __restrict
                      grad_image, grad_t, g2d);
 }
 
+// ---------------------------------------------------------------- batched
+// Work queue of a batched render: every (camera, tile) job, the longest
+// lists first (log2 buckets), so the persistent blend finishes on short jobs.
+__global__ void __launch_bounds__(1024) build_queue_kernel(const int2* __restrict__ ranges, int total_tiles,
+                                                           uint32_t* __restrict__ queue, unsigned* job_ctr) {
+  __shared__ unsigned s_cnt[33];
+  __shared__ unsigned s_off[33];
+  if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
+  if (threadIdx.x == 0) *job_ctr = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < total_tiles; t += blockDim.x) {
+    const int2 rg = ranges[t];
+    const unsigned len = (unsigned)max(rg.y - rg.x, 0);
+    atomicAdd(&s_cnt[__clz(len)], 1u);  // bucket 0 holds the longest lists
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+    for (int b = 0; b < 33; ++b) {
+      s_off[b] = run;
+      run += s_cnt[b];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < total_tiles; t += blockDim.x) {
+    const int2 rg = ranges[t];
+    const unsigned len = (unsigned)max(rg.y - rg.x, 0);
+    queue[atomicAdd(&s_off[__clz(len)], 1u)] = (uint32_t)t;
+  }
+}
+
+// Persistent forward blend over the job queue of all cameras: each CTA takes
+// the next job with an atomic ticket until the queue is empty.
+template <int KID, int PPT>
+__global__ void __launch_bounds__(128) blend_batch_kernel(const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
+                                                          const int2* __restrict__ ranges, const CamTable cams,
+                                                          const BatchPix pix, const ParDev P,
+                                                          const uint32_t* __restrict__ queue, int n_jobs,
+                                                          unsigned* job_ctr, float* __restrict__ images,
+                                                          float* __restrict__ t_final, int B) {
+  extern __shared__ float4 smem[];
+  __shared__ int s_job;
+  __shared__ int s_base[LS_MAX_CAMS];
+  const int nc = cams.n;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) s_base[c] = cams.c[c].tile_base;
+  for (;;) {
+    __syncthreads();  // the previous job is done with shared memory and s_job
+    if (threadIdx.x == 0) s_job = (int)atomicAdd(job_ctr, 1u);
+    __syncthreads();
+    const int job = s_job;
+    if (job >= n_jobs) break;
+    const int gt = (int)queue[job];
+    int lo = 0, hi = nc - 1;  // camera: last tile_base <= gt
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_base[mid] <= gt) lo = mid;
+      else hi = mid - 1;
+    }
+    const CamDev& cam = cams.c[lo];
+    const int tile = gt - cam.tile_base;
+    TileJob J;
+    J.x0 = (tile % cam.tiles_x) * P.tile_w;
+    J.y0 = (tile / cam.tiles_x) * P.tile_h;
+    J.W = cam.W;
+    J.H = cam.H;
+    J.rg = ranges[gt];
+    J.pix_base = pix.base[lo];
+    fwd_tile<KID, PPT, false>(rec, vals, P, J, smem, smem + B, smem + 2 * B, B, images, t_final, nullptr, nullptr);
+  }
+}
+
 }  // namespace
 
 // Pixels per thread: 4 for tiles of 256+ pixels, 2 for 8x8 (one warp).
@@ -448,6 +519,52 @@ cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev&
   }
 #undef LS_BB
 #undef LS_BB2
+  return cudaGetLastError();
+}
+
+}  // namespace ls
+
+namespace ls {
+
+cudaError_t launch_build_queue(const int32_t* ranges, int total_tiles, uint32_t* queue, unsigned* job_ctr,
+                               cudaStream_t st) {
+  build_queue_kernel<<<1, 1024, 0, st>>>(reinterpret_cast<const int2*>(ranges), total_tiles, queue, job_ctr);
+  return cudaGetLastError();
+}
+
+// Persistent grid: as many CTAs as fit on the device at once.
+cudaError_t launch_blend_batch(const float4* rec, const uint32_t* vals, const int32_t* ranges, const CamTable& cams,
+                              const BatchPix& pix, const ParDev& P, const uint32_t* queue, int n_jobs,
+                              unsigned* job_ctr, float* images, float* t_final, int batch, cudaStream_t st) {
+  const int ppt = ppt_for(P);
+  const int threads = P.tile_w * P.tile_h / ppt;
+  const int B = batch > 0 ? batch : 4 * threads;
+  const size_t sm = sizeof(float4) * 3 * B;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+#define LS_BB3(K, PP)                                                                                               \
+  do {                                                                                                              \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blend_batch_kernel<K, PP>, threads, sm);             \
+    if (e != cudaSuccess) return e;                                                                                 \
+    blend_batch_kernel<K, PP><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), threads, sm, st>>>(                    \
+        rec, vals, reinterpret_cast<const int2*>(ranges), cams, pix, P, queue, n_jobs, job_ctr, images, t_final, B); \
+  } while (0)
+#define LS_BB(K)                \
+  do {                          \
+    if (ppt == 4) LS_BB3(K, 4); \
+    else LS_BB3(K, 2);          \
+  } while (0)
+  switch (P.kernel) {
+    case LS_KERNEL_GAUSSIAN: LS_BB(LS_KERNEL_GAUSSIAN); break;
+    case LS_KERNEL_LAPLACIAN: LS_BB(LS_KERNEL_LAPLACIAN); break;
+    case LS_KERNEL_COSINE: LS_BB(LS_KERNEL_COSINE); break;
+    case LS_KERNEL_QUADRATIC: LS_BB(LS_KERNEL_QUADRATIC); break;
+    default: LS_BB(LS_KERNEL_LINEAR); break;
+  }
+#undef LS_BB
+#undef LS_BB3
   return cudaGetLastError();
 }
 

@@ -64,6 +64,15 @@ cudaError_t launch_dup_emit(int64_t R, const uint32_t* order, const uint2* rect_
                             uint32_t* vals, int key_passes, uint32_t* tile_hist, cudaStream_t st);
 
 // ---- blending (blend.cu)
+// Pixel offset of each camera's image in a batched render's packed output.
+struct BatchPix {
+  size_t base[LS_MAX_CAMS];
+};
+cudaError_t launch_build_queue(const int32_t* ranges, int total_tiles, uint32_t* queue, unsigned* job_ctr,
+                               cudaStream_t st);
+cudaError_t launch_blend_batch(const float4* rec, const uint32_t* vals, const int32_t* ranges, const CamTable& cams,
+                              const BatchPix& pix, const ParDev& P, const uint32_t* queue, int n_jobs,
+                              unsigned* job_ctr, float* images, float* t_final, int batch, cudaStream_t st);
 cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
                              const uint32_t* vals, float* image, float* t_final, int32_t* n_last,
                              unsigned long long* stats, cudaStream_t st);
