@@ -187,6 +187,45 @@ ls_status ls_render_bwd(int32_t n, const float* means, const float* scales, cons
                         float* g_sh, float* g2d_out, void* workspace, size_t ws_bytes, int32_t* status_dev,
                         void* stream);
 
+/* ---- a8: learned termination --------------------------------------------
+ * A per-tile MLP 48 -> 64 -> 64 -> 1 (ReLU) with FP16 inputs and weights and
+ * FP32 accumulation (tensor cores) predicts the log camera depth at which
+ * every pixel of the tile has stopped.  Inputs: LS_MLP_FEATURES = 35 used
+ * features of a 48-wide FP16 row (the rest zero).  Parameters, packed FP32
+ * (master copy and gradients, LS_MLP_NPARAM floats):
+ *   w1t [64][48] | b1 [64] | w2t [64][64] | b2 [64] | w3 [64] | b3 [1]
+ * (w1t, w2t are [out][in]).  The forward reads FP16 copies of w1t, w2t, w3
+ * and FP32 biases through ls_mlp (device pointers). */
+#define LS_MLP_IN 48
+#define LS_MLP_HID 64
+#define LS_MLP_FEATURES 35
+#define LS_MLP_NPARAM 7361
+typedef struct {
+  const void* w1t;  /* fp16 [64][48] */
+  const float* b1;  /* [64] */
+  const void* w2t;  /* fp16 [64][64] */
+  const float* b2;  /* [64] */
+  const void* w3;   /* fp16 [64] */
+  const float* b3;  /* [1] */
+} ls_mlp;
+
+/* y [m] = MLP(x [m][48] fp16).  Tensor-core forward. */
+ls_status ls_mlp_forward(int64_t m, const void* x, const ls_mlp* net, float* y, void* stream);
+
+/* Gradient of the mean asymmetric squared error
+ *   (1/m) sum_r w_r (y_r - target_r)^2,  w_r = under_weight if y_r < target_r else 1,
+ * ACCUMULATED into grad [LS_MLP_NPARAM] (packed layout) and, when not NULL,
+ * the loss into *loss.  Tensor-core backward (layer inputs rounded to fp16 as
+ * in the forward; the rounding is passed through as identity). */
+ls_status ls_mlp_backward(int64_t m, const void* x, const ls_mlp* net, const float* target, float under_weight,
+                          float* grad, float* loss, void* stream);
+
+/* One Adam step (bias-corrected, step >= 1) on the packed FP32 master
+ * parameters with moments m1, m2, then refresh of the FP16 weights and FP32
+ * biases pointed to by net (which must be writable device memory). */
+ls_status ls_mlp_adam(int32_t step, float lr, float beta1, float beta2, float eps, float* master, const float* grad,
+                      float* m1, float* m2, const ls_mlp* net, void* stream);
+
 /* Workspace of ls_render_batch in bytes (projected records, keys, ranges,
  * job queue and the duplicate/sort scratch). */
 size_t ls_render_batch_workspace(int32_t n, const ls_camera* cams, int32_t n_cams, const ls_params* params,

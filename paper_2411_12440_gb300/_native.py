@@ -30,6 +30,11 @@ class LsParams(ctypes.Structure):
                 ("far_plane", ctypes.c_float), ("sh_degree", ctypes.c_int32)]
 
 
+class LsMlp(ctypes.Structure):
+    _fields_ = [("w1t", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("w2t", ctypes.c_void_p),
+                ("b2", ctypes.c_void_p), ("w3", ctypes.c_void_p), ("b3", ctypes.c_void_p)]
+
+
 class LsCamera(ctypes.Structure):
     _fields_ = [("viewmat", ctypes.c_float * 16), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
                 ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
@@ -57,6 +62,10 @@ PROTOTYPES = {
     "ls_project_bwd": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _I32, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ls_render_bwd_workspace": (_SZ, [_I64]),
     "ls_render_batch_workspace": (_SZ, [_I32, _PC, _I32, _PP, _I64]),
+    "ls_mlp_forward": (_I32, [_I64, _P, ctypes.POINTER(LsMlp), _P, _P]),
+    "ls_mlp_backward": (_I32, [_I64, _P, ctypes.POINTER(LsMlp), _P, ctypes.c_float, _P, _P, _P]),
+    "ls_mlp_adam": (_I32, [_I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P,
+                           ctypes.POINTER(LsMlp), _P]),
     "ls_render_batch": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _I32, _PP, _I32, _I64, _P, _P, _P, _P, _SZ, _P, _P]),
     "ls_render_bwd": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                              _P, _P, _P, _SZ, _P, _P]),

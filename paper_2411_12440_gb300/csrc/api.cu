@@ -432,4 +432,36 @@ ls_status ls_render_batch(int32_t n, const float* means, const float* scales, co
   return LS_OK;
 }
 
+// ---------------------------------------------------------------- termination MLP
+namespace {
+bool mlp_ok(const ls_mlp* n) { return n && n->w1t && n->b1 && n->w2t && n->b2 && n->w3 && n->b3; }
+MlpDev mlp_dev(const ls_mlp* n) { return MlpDev{n->w1t, n->b1, n->w2t, n->b2, n->w3, n->b3}; }
+}  // namespace
+
+ls_status ls_mlp_forward(int64_t m, const void* x, const ls_mlp* net, float* y, void* stream) {
+  if (m < 0 || !mlp_ok(net)) return LS_ERR_INVALID_ARG;
+  if (m > 0 && (!x || !y)) return LS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(x) % 16) return LS_ERR_INVALID_ARG;
+  LS_TRY(launch_mlp_forward(m, x, mlp_dev(net), y, static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+ls_status ls_mlp_backward(int64_t m, const void* x, const ls_mlp* net, const float* target, float under_weight,
+                          float* grad, float* loss, void* stream) {
+  if (m < 0 || !mlp_ok(net) || !grad || !(under_weight > 0.f)) return LS_ERR_INVALID_ARG;
+  if (m > 0 && (!x || !target)) return LS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(x) % 16) return LS_ERR_INVALID_ARG;
+  LS_TRY(launch_mlp_backward(m, x, mlp_dev(net), target, under_weight, grad, loss, static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+ls_status ls_mlp_adam(int32_t step, float lr, float beta1, float beta2, float eps, float* master, const float* grad,
+                      float* m1, float* m2, const ls_mlp* net, void* stream) {
+  if (step < 1 || !mlp_ok(net) || !master || !grad || !m1 || !m2) return LS_ERR_INVALID_ARG;
+  MlpMut w{const_cast<void*>(net->w1t), const_cast<float*>(net->b1), const_cast<void*>(net->w2t),
+           const_cast<float*>(net->b2), const_cast<void*>(net->w3), const_cast<float*>(net->b3)};
+  LS_TRY(launch_mlp_adam(step, lr, beta1, beta2, eps, master, grad, m1, m2, w, static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
 }  // extern "C"

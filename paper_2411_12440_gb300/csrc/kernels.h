@@ -80,4 +80,27 @@ cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev&
                              const uint32_t* vals, const float* t_final, const int32_t* n_last,
                              const float* grad_image, const float* grad_t, float* g2d, cudaStream_t st);
 
+// ---- termination MLP (mlp.cu)
+struct MlpDev {
+  const void* w1t;
+  const float* b1;
+  const void* w2t;
+  const float* b2;
+  const void* w3;
+  const float* b3;
+};
+struct MlpMut {
+  void* w1t;
+  float* b1;
+  void* w2t;
+  float* b2;
+  void* w3;
+  float* b3;
+};
+cudaError_t launch_mlp_forward(int64_t m, const void* x, const MlpDev& net, float* y, cudaStream_t st);
+cudaError_t launch_mlp_backward(int64_t m, const void* x, const MlpDev& net, const float* target, float under_weight,
+                                float* grad, float* loss, cudaStream_t st);
+cudaError_t launch_mlp_adam(int step, float lr, float beta1, float beta2, float eps, float* master, const float* grad,
+                            float* m1, float* m2, const MlpMut& net, cudaStream_t st);
+
 }  // namespace ls

@@ -249,3 +249,32 @@ def loss_weights(height, width, seed):
     """Seeded weights w [H, W, 3] and v [H, W] of the test loss <w, C> + <v, T>."""
     rng = np.random.default_rng(seed)
     return _f32(rng.standard_normal((height, width, 3))), _f32(rng.standard_normal((height, width)))
+
+
+def random_mlp_params(seed, n_param=7361, n_in=48, hid=64, features=35):
+    """Random packed parameters of the 48 -> 64 -> 64 -> 1 termination MLP
+    (w1t [64][48] | b1 | w2t [64][64] | b2 | w3 | b3) and nothing else."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros(n_param)
+    o = 0
+    p[o:o + hid * n_in] = rng.normal(0, np.sqrt(2.0 / features), hid * n_in)
+    o += hid * n_in
+    p[o:o + hid] = rng.normal(0, 0.05, hid)
+    o += hid
+    p[o:o + hid * hid] = rng.normal(0, np.sqrt(2.0 / hid), hid * hid)
+    o += hid * hid
+    p[o:o + hid] = rng.normal(0, 0.05, hid)
+    o += hid
+    p[o:o + hid] = rng.normal(0, np.sqrt(1.0 / hid), hid)
+    o += hid
+    p[o] = 0.3
+    return p
+
+
+def random_mlp_batch(m, seed, n_in=48, features=35):
+    """Random feature rows (half precision, zero past `features`) and targets."""
+    rng = np.random.default_rng(seed)
+    x = np.zeros((m, n_in), np.float16)
+    x[:, :features] = rng.uniform(-1.0, 2.0, (m, features)).astype(np.float16)
+    t = rng.normal(1.0, 0.7, m)
+    return x, t
