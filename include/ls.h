@@ -148,7 +148,12 @@ ls_status ls_render_fwd(const void* proj, int64_t n_records, const ls_camera* ca
  * to size the roofline of the blending kernels, not on the hot path). */
 ls_status ls_render_stats(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
                           const int32_t* tile_ranges, const uint32_t* vals, float* image, float* t_final,
-                          int32_t* n_last, uint64_t* stats_dev, int32_t* status_dev, void* stream);
+                          int32_t* n_last, uint64_t* stats_dev, float* tile_labels, int32_t* status_dev,
+                          void* stream);
+/* tile_labels [tiles] (or NULL): per tile, the camera depth of the list entry
+ * at which its last pixel stopped (every later entry is never needed), +inf
+ * when some pixel never stops, 0 for an empty tile: the target of the
+ * learned termination. */
 
 /* a5: adjoint of ls_render_fwd with respect to each record's (mx, my, a, b,
  * c, o_eff, r, g, b), recomputing T back to front from t_final / n_last
@@ -225,6 +230,37 @@ ls_status ls_mlp_backward(int64_t m, const void* x, const ls_mlp* net, const flo
  * biases pointed to by net (which must be writable device memory). */
 ls_status ls_mlp_adam(int32_t step, float lr, float beta1, float beta2, float eps, float* master, const float* grad,
                       float* m1, float* m2, const ls_mlp* net, void* stream);
+
+/* Per-tile inputs of the termination MLP for one camera, from projected
+ * records.  Each visible record whose support box covers the tile adds its
+ * expected coverage w = (o_eff / 3) min(1, ellipse area / box area) to its
+ * log-depth bin (32 bins, edges 0.5 * 64^(i/32), i = 1..31).  features
+ * [tiles][48] fp16 = log1p of the coverage summed over bins 0..b (b = 0..31),
+ * then the world direction of the ray through the tile centre (3), then
+ * zeros; tile_total [tiles] = number of records covering the tile.
+ * workspace: ls_tile_features_workspace bytes. */
+size_t ls_tile_features_workspace(const ls_camera* cam, const ls_params* params);
+ls_status ls_tile_features(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                           void* features, int32_t* tile_total, void* workspace, size_t ws_bytes, void* stream);
+
+/* a8: forward render of one camera with learned termination.  The MLP (or,
+ * when mlp is NULL, the caller's per-tile depths dstar_in [tiles]) proposes
+ * per tile a depth d* = exp(MLP + margin); only keys with depth <= d* are
+ * sorted and blended.  A tile is final when every pixel stopped or has
+ * T < t_thr, or when it has no held-out keys; otherwise it is refuted and
+ * blending resumes over its held-out keys from the stored per-pixel state.
+ * With t_thr <= params->t_min the image equals ls_render_fwd's bit for bit;
+ * with a larger t_thr each pixel is within t_thr (max rgb + bg) of it.
+ * Outputs as ls_render_fwd (n_last continues into the held-out lists),
+ * dstar_out [tiles] (or NULL), stats_dev [4] (int64, device): keys before
+ * truncation, kept keys, held-out keys sorted for refuted tiles, refuted
+ * tiles.  key_capacity bounds both the kept and the held-out keys. */
+size_t ls_render_learned_workspace(int32_t n, const ls_camera* cam, const ls_params* params, int64_t key_capacity);
+ls_status ls_render_learned(int32_t n, const float* means, const float* scales, const float* quats,
+                            const float* opacities, const float* sh, const ls_camera* cam, const ls_params* params,
+                            const ls_mlp* mlp, float margin, const float* dstar_in, float t_thr, int64_t key_capacity,
+                            float* image, float* t_final, int32_t* n_last, float* dstar_out, int64_t* stats_dev,
+                            void* workspace, size_t ws_bytes, int32_t* status_dev, void* stream);
 
 /* Workspace of ls_render_batch in bytes (projected records, keys, ranges,
  * job queue and the duplicate/sort scratch). */

@@ -113,7 +113,8 @@ def _window(window):
 
 def render(proj, vis, width, height, params=None, rule_f32=False, dkey=None, brute=False, window=None):
     """Front-to-back composite (Eq. 6) of projected records; `window` =
-    (x0, x1, y0, y1) restricts it to those pixels (others stay zero)."""
+    (x0, x1, y0, y1) restricts it to those pixels (others stay zero).
+    Also returns per-tile termination depths `labels` (tiled mode)."""
     n = proj.shape[0]
     proj = _d(proj)
     vis8 = np.ascontiguousarray(vis, dtype=np.uint8)
@@ -125,12 +126,30 @@ def render(proj, vis, width, height, params=None, rule_f32=False, dkey=None, bru
     stats = np.zeros(2, dtype=np.int64)
     dk = None if dkey is None else np.ascontiguousarray(dkey, dtype=np.uint32)
     wp, _keep = _window(window)
+    Pd = dict(DEFAULTS)
+    Pd.update(params or {})
+    tiles = ((width + Pd["tile_w"] - 1) // Pd["tile_w"]) * ((height + Pd["tile_h"] - 1) // Pd["tile_h"])
+    labels = np.zeros(tiles)
     lib().lso_render(ctypes.c_int(n), _p(proj), _p(vis8), ctypes.c_int(width), ctypes.c_int(height),
                      _p(params_array(params)), ctypes.c_int(int(rule_f32)),
                      _p(dk) if dk is not None else ctypes.c_void_p(0), ctypes.c_int(int(brute)), _p(img), _p(T),
-                     _p(n_last), _p(last_id), _p(flags), _p(stats), wp)
+                     _p(n_last), _p(last_id), _p(flags), _p(stats), wp, _p(labels))
     return dict(image=img, T=T, n_last=n_last, last_id=last_id, flags=flags.astype(bool), n_eval=int(stats[0]),
-                n_contrib=int(stats[1]))
+                n_contrib=int(stats[1]), labels=labels)
+
+
+def tile_depth_hist(foot, dkey, proj, width, height, tile_w, tile_h):
+    """Per-tile inputs of the termination network: (counts [tiles], cumulative
+    coverage [tiles, 32]) of binary32 footprints; proj [R, NP] supplies each
+    record's opacity, squared support radius and conic."""
+    R = foot.shape[0]
+    tiles = ((width + tile_w - 1) // tile_w) * ((height + tile_h - 1) // tile_h)
+    counts = np.zeros(tiles, dtype=np.int32)
+    cov = np.zeros((tiles, 32))
+    lib().lso_tile_depth_hist(ctypes.c_longlong(R), _p(np.ascontiguousarray(foot, np.float32)),
+                              _p(np.ascontiguousarray(dkey, np.uint32)), _p(_d(proj)), ctypes.c_int(width),
+                              ctypes.c_int(height), ctypes.c_int(tile_w), ctypes.c_int(tile_h), _p(counts), _p(cov))
+    return counts, cov
 
 
 def render_bwd(proj, vis, width, height, gC, gT, params=None, rule_f32=False, dkey=None, window=None):

@@ -539,6 +539,44 @@ long long lso_dupsort_f32(long long R, const float* foot, const uint32_t* dkey, 
   return K;
 }
 
+// Per-tile inputs of the termination network from binary32 footprints foot
+// [R][4] and depth bits dkey, with each record's opacity, squared support
+// radius and conic taken from proj [R][NP]: counts [tiles] = records whose
+// support box covers the tile; coverage [tiles][32] = for bin b, the summed
+// expected coverage o/3 * min(1, support-ellipse area / box area) of those
+// records in bins 0..b.  Bin i holds depths in [e_i, e_{i+1}), e_i =
+// binary32(0.5 * 64^(i/32)), i = 1..31 (bin 0 below e_1, bin 31 from e_31).
+void lso_tile_depth_hist(long long R, const float* foot, const uint32_t* dkey, const double* proj, int W, int H,
+                         int TW, int TH, int32_t* counts, double* coverage) {
+  int tx_n = (W + TW - 1) / TW, ty_n = (H + TH - 1) / TH;
+  float edge[31];
+  for (int i = 0; i < 31; ++i) edge[i] = (float)(0.5 * std::pow(64.0, (i + 1) / 32.0));
+  for (int t = 0; t < tx_n * ty_n; ++t) {
+    counts[t] = 0;
+    for (int b = 0; b < 32; ++b) coverage[32 * t + b] = 0.0;
+  }
+  for (long long r = 0; r < R; ++r) {
+    if (dkey[r] == 0xFFFFFFFFu) continue;
+    Rect rc = rect_f32(foot[4 * r], foot[4 * r + 1], foot[4 * r + 2], foot[4 * r + 3], W, H);
+    if (rc.empty) continue;
+    float d;
+    std::memcpy(&d, &dkey[r], 4);
+    int b = 0;
+    while (b < 31 && d >= edge[b]) ++b;
+    const double* p = proj + (size_t)r * NP;
+    const double detA = p[P_A] * p[P_C] - p[P_B] * p[P_B];
+    const double ellipse = PI * p[P_RHO2] / std::sqrt(detA);
+    const int tx0 = rc.x0 / TW, tx1 = rc.x1 / TW, ty0 = rc.y0 / TH, ty1 = rc.y1 / TH;
+    const double box = (double)(tx1 - tx0 + 1) * (ty1 - ty0 + 1) * TW * TH;
+    const double w = p[P_O] / 3.0 * std::min(1.0, ellipse / box);
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        counts[ty * tx_n + tx]++;
+        for (int bb = b; bb < 32; ++bb) coverage[(ty * tx_n + tx) * 32 + bb] += w;
+      }
+  }
+}
+
 // Forward render of projected records proj [n][NP] (Eq. 6).  brute = 1 skips
 // the tiles: every pixel runs over all visible records in (depth, id) order.
 // rule_f32 / dkey select the binary32 tile rule and sort bits (dkey may be
@@ -548,7 +586,7 @@ long long lso_dupsort_f32(long long R, const float* foot, const uint32_t* dkey, 
 // {x0, x1, y0, y1}, only pixels in [x0, x1) x [y0, y1) are composited.
 int lso_render(int n, const double* proj, const unsigned char* vis, int W, int H, const double* parv,
                int rule_f32, const uint32_t* dkey, int brute, double* image, double* T, int32_t* n_last,
-               int32_t* last_id, unsigned char* flags, long long* stats, const int32_t* window) {
+               int32_t* last_id, unsigned char* flags, long long* stats, const int32_t* window, double* labels) {
   Par P = unpack_par(parv);
   // pixel window [x0, x1) x [y0, y1); pixels outside it are left untouched
   int wx0 = window ? window[0] : 0, wx1 = window ? window[1] : W;
@@ -581,10 +619,13 @@ int lso_render(int n, const double* proj, const unsigned char* vis, int W, int H
 #pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1) reduction(+ : n_eval, n_contrib)
   for (int t = 0; t < ntiles; ++t) {
     int tx = t % Ls.tiles_x, ty = t / Ls.tiles_x;
-    int emax = 0, npix = 0;
+    int emax = 0, npix = 0, smax = -1;
+    bool never = false;
     for (int py = std::max(ty * P.tile_h, wy0); py < std::min(std::min(H, (ty + 1) * P.tile_h), wy1); ++py)
       for (int px = std::max(tx * P.tile_w, wx0); px < std::min(std::min(W, (tx + 1) * P.tile_w), wx1); ++px) {
         PixOut o = blend_pixel(Ls.L[t], proj, px + 0.5, py + 0.5, P, nullptr);
+        if (o.stop_index >= (int)Ls.L[t].size()) never = true;
+        else smax = std::max(smax, o.stop_index);
         size_t pi = (size_t)py * W + px;
         for (int c = 0; c < 3; ++c) image[3 * pi + c] = o.C[c] + o.T * P.bg[c];
         T[pi] = o.T;
@@ -597,6 +638,13 @@ int lso_render(int n, const double* proj, const unsigned char* vis, int W, int H
         ++npix;
       }
     n_eval += (long long)emax * npix;
+    // termination depth of the tile: depth of the entry at which its last
+    // pixel stopped; +inf if a pixel never stops; 0 for an empty list
+    if (labels) {
+      if (Ls.L[t].empty() || npix == 0) labels[t] = 0.0;
+      else if (never) labels[t] = INFINITY;
+      else labels[t] = proj[(size_t)Ls.L[t][smax] * NP + P_DEPTH];
+    }
   }
   stats[0] = n_eval;
   stats[1] = n_contrib;

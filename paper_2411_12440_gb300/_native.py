@@ -57,7 +57,10 @@ PROTOTYPES = {
     "ls_duplicate_sort": (_I32, [_I64, _P, _PC, _I32, _PP, _I64, _P, _P, _P, _P, _P, _SZ, _P, _P]),
     "ls_duplicate_sort_noalloc": (_I32, [_I64, _P, _PC, _I32, _PP, _I64, _P, _P, _P, _P, _P, _P]),
     "ls_render_fwd": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _P, _P, _P, _P]),
-    "ls_render_stats": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ls_render_stats": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ls_tile_features_workspace": (_SZ, [_PC, _PP]),
+    "ls_tile_features": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _SZ, _P]),
+    "ls_render_learned_workspace": (_SZ, [_I32, _PC, _PP, _I64]),
     "ls_blend_bwd": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ls_project_bwd": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _I32, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ls_render_bwd_workspace": (_SZ, [_I64]),
@@ -66,6 +69,8 @@ PROTOTYPES = {
     "ls_mlp_backward": (_I32, [_I64, _P, ctypes.POINTER(LsMlp), _P, ctypes.c_float, _P, _P, _P]),
     "ls_mlp_adam": (_I32, [_I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P,
                            ctypes.POINTER(LsMlp), _P]),
+    "ls_render_learned": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _PP, ctypes.POINTER(LsMlp), ctypes.c_float, _P,
+                                 ctypes.c_float, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P, _P]),
     "ls_render_batch": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _I32, _PP, _I32, _I64, _P, _P, _P, _P, _SZ, _P, _P]),
     "ls_render_bwd": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                              _P, _P, _P, _SZ, _P, _P]),

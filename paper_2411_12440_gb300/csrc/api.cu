@@ -271,7 +271,8 @@ ls_status ls_render_fwd(const void* proj, int64_t n_records, const ls_camera* ca
 
 ls_status ls_render_stats(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
                           const int32_t* tile_ranges, const uint32_t* vals, float* image, float* t_final,
-                          int32_t* n_last, uint64_t* stats_dev, int32_t* status_dev, void* stream) {
+                          int32_t* n_last, uint64_t* stats_dev, float* tile_labels, int32_t* status_dev,
+                          void* stream) {
   if (!params_ok(params) || n_records < 0) return LS_ERR_INVALID_ARG;
   CamTable T;
   if (!make_cams(cam, 1, params, T, nullptr)) return LS_ERR_INVALID_ARG;
@@ -281,7 +282,7 @@ ls_status ls_render_stats(const void* proj, int64_t n_records, const ls_camera* 
   ProjCPtr pp = proj_cplanes(proj, n_records);
   LS_TRY(launch_blend_fwd(pp.rec, T.c[0], make_par(params), reinterpret_cast<const int2*>(tile_ranges), vals, image,
                           t_final, n_last, reinterpret_cast<unsigned long long*>(stats_dev),
-                          static_cast<cudaStream_t>(stream)));
+                          static_cast<cudaStream_t>(stream), tile_labels));
   return LS_OK;
 }
 
@@ -461,6 +462,226 @@ ls_status ls_mlp_adam(int32_t step, float lr, float beta1, float beta2, float ep
   MlpMut w{const_cast<void*>(net->w1t), const_cast<float*>(net->b1), const_cast<void*>(net->w2t),
            const_cast<float*>(net->b2), const_cast<void*>(net->w3), const_cast<float*>(net->b3)};
   LS_TRY(launch_mlp_adam(step, lr, beta1, beta2, eps, master, grad, m1, m2, w, static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+// ---------------------------------------------------------------- learned termination
+namespace {
+
+struct LearnedWs {
+  char* proj;
+  uint32_t *dk_a, *dv_a, *dk_b, *dv_b;
+  uint2* rect;
+  uint32_t* block_sums;
+  int* diff;
+  int32_t* tile_total;
+  void* x16;
+  float* y;
+  uint32_t* dstar_bits;
+  uint8_t* refuted;
+  uint32_t *wc_kept, *wc_held;
+  uint32_t *k_keys, *k_vals, *k_alt_keys, *k_alt_vals;
+  uint32_t *h_keys, *h_vals, *h_alt_keys, *h_alt_vals;
+  int32_t *k_ranges, *h_ranges;
+  int64_t *n_kept, *n_kept_valid, *n_held, *n_held_valid;
+  unsigned* n_refuted;
+  unsigned long long* key_total;
+  size_t zero_begin, zero_bytes;
+  char *depth_scratch, *kept_scratch, *held_scratch;
+  size_t total;
+};
+
+LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int tiles_y, int kp) {
+  LearnedWs w;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base + off;
+    off += al256(bytes);
+    return p;
+  };
+  const size_t Rz = (size_t)(R > 0 ? R : 1), Cz = (size_t)(cap > 0 ? cap : 1);
+  const size_t tiles = (size_t)tiles_x * tiles_y, nb = (Rz + DUP_BLOCK - 1) / DUP_BLOCK;
+  w.proj = take(ls_proj_bytes((int64_t)Rz));
+  w.dk_a = reinterpret_cast<uint32_t*>(take(4 * Rz));
+  w.dv_a = reinterpret_cast<uint32_t*>(take(4 * Rz));
+  w.dk_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
+  w.dv_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
+  w.rect = reinterpret_cast<uint2*>(take(8 * Rz));
+  w.block_sums = reinterpret_cast<uint32_t*>(take(4 * nb));
+  w.tile_total = reinterpret_cast<int32_t*>(take(4 * tiles));
+  w.x16 = take(2 * LS_MLP_IN * tiles);
+  w.y = reinterpret_cast<float*>(take(4 * tiles));
+  w.dstar_bits = reinterpret_cast<uint32_t*>(take(4 * tiles));
+  w.wc_kept = reinterpret_cast<uint32_t*>(take(4 * nb * (DUP_THREADS / 32)));
+  w.wc_held = reinterpret_cast<uint32_t*>(take(4 * nb * (DUP_THREADS / 32)));
+  w.k_keys = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.k_vals = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.k_alt_keys = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.k_alt_vals = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.h_keys = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.h_vals = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.h_alt_keys = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.h_alt_vals = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.k_ranges = reinterpret_cast<int32_t*>(take(8 * tiles));
+  w.h_ranges = reinterpret_cast<int32_t*>(take(8 * tiles));
+  // cleared before every call
+  w.zero_begin = off;
+  w.diff = reinterpret_cast<int*>(take(4 * 33 * (size_t)(tiles_x + 1) * (tiles_y + 1)));
+  w.refuted = reinterpret_cast<uint8_t*>(take(tiles));
+  w.n_kept = reinterpret_cast<int64_t*>(take(8));
+  w.n_kept_valid = reinterpret_cast<int64_t*>(take(8));
+  w.n_held = reinterpret_cast<int64_t*>(take(8));
+  w.n_held_valid = reinterpret_cast<int64_t*>(take(8));
+  w.n_refuted = reinterpret_cast<unsigned*>(take(4));
+  w.key_total = reinterpret_cast<unsigned long long*>(take(8));
+  w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4));
+  w.kept_scratch = take(sort_scratch_bytes((int64_t)Cz, kp));
+  w.held_scratch = take(sort_scratch_bytes((int64_t)Cz, kp));
+  w.zero_bytes = off - w.zero_begin;
+  w.total = off;
+  return w;
+}
+
+// Sort `n_dev` keys (ek, ev) by tile in kp passes so that the result lands in
+// (keys, vals); the last pass records the ranges.
+ls_status tile_sort(uint32_t* ek, uint32_t* ev, uint32_t* ok, uint32_t* ov, const int64_t* n_dev, int64_t cap, int kp,
+                    const SortScratch& ss, int32_t* ranges, int tiles, int32_t* status, cudaStream_t st) {
+  LS_TRY(launch_radix_scan(ss.hist, kp, st));
+  for (int p = 0; p < kp; ++p) {
+    LS_TRY(launch_onesweep_pass(ek, ev, ok, ov, n_dev, 0, cap, 0, p, ss, p == kp - 1 ? ranges : nullptr, status, st));
+    std::swap(ek, ok);
+    std::swap(ev, ov);
+  }
+  LS_TRY(launch_ranges_fixup(ranges, tiles, st));
+  return LS_OK;
+}
+
+}  // namespace
+
+size_t ls_tile_features_workspace(const ls_camera* cam, const ls_params* params) {
+  if (!params_ok(params)) return 0;
+  CamTable T;
+  if (!make_cams(cam, 1, params, T, nullptr)) return 0;
+  return al256(hist_planes_bytes(T.c[0]));
+}
+
+ls_status ls_tile_features(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                           void* features, int32_t* tile_total, void* workspace, size_t ws_bytes, void* stream) {
+  if (!params_ok(params) || n_records < 0) return LS_ERR_INVALID_ARG;
+  CamTable T;
+  if (!make_cams(cam, 1, params, T, nullptr)) return LS_ERR_INVALID_ARG;
+  if (!features || !tile_total || !workspace || ws_bytes < ls_tile_features_workspace(cam, params))
+    return LS_ERR_INVALID_ARG;
+  if (n_records > 0 && !proj) return LS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return LS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ParDev P = make_par(params);
+  LS_TRY(cudaMemsetAsync(workspace, 0, ls_tile_features_workspace(cam, params), st));
+  ProjCPtr pp = proj_cplanes(proj, n_records);
+  LS_TRY(launch_tile_hist(n_records, pp.rec, pp.foot, pp.dkey, T.c[0], P, workspace, st));
+  LS_TRY(launch_features(workspace, T.c[0], P, features, tile_total, nullptr, st));
+  return LS_OK;
+}
+
+size_t ls_render_learned_workspace(int32_t n, const ls_camera* cam, const ls_params* params, int64_t key_capacity) {
+  if (n < 0 || key_capacity < 0 || !params_ok(params)) return 0;
+  CamTable T;
+  int64_t tiles = 0;
+  if (!make_cams(cam, 1, params, T, &tiles)) return 0;
+  return learned_layout(nullptr, n, key_capacity, T.c[0].tiles_x, T.c[0].tiles_y, key_passes_for(tiles)).total;
+}
+
+ls_status ls_render_learned(int32_t n, const float* means, const float* scales, const float* quats,
+                            const float* opacities, const float* sh, const ls_camera* cam, const ls_params* params,
+                            const ls_mlp* mlp, float margin, const float* dstar_in, float t_thr, int64_t key_capacity,
+                            float* image, float* t_final, int32_t* n_last, float* dstar_out, int64_t* stats_dev,
+                            void* workspace, size_t ws_bytes, int32_t* status_dev, void* stream) {
+  if (n < 0 || !params_ok(params) || !(t_thr >= 0.f)) return LS_ERR_INVALID_ARG;
+  CamTable T;
+  int64_t tiles64 = 0;
+  if (!make_cams(cam, 1, params, T, &tiles64)) return LS_ERR_INVALID_ARG;
+  if (key_capacity < 0 || key_capacity > 0x7FFFFFFFll) return LS_ERR_INVALID_ARG;
+  if (!image || !t_final || !n_last || !stats_dev || !workspace) return LS_ERR_INVALID_ARG;
+  if (mlp ? !mlp_ok(mlp) : !dstar_in) return LS_ERR_INVALID_ARG;
+  if (n > 0 && (!means || !scales || !quats || !opacities || !sh)) return LS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(quats) % 16 || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return LS_ERR_INVALID_ARG;
+  const CamDev& C = T.c[0];
+  const int tiles = (int)tiles64, kp = key_passes_for(tiles64);
+  const int64_t R = n;
+  LearnedWs w = learned_layout(static_cast<char*>(workspace), R, key_capacity, C.tiles_x, C.tiles_y, kp);
+  if (ws_bytes < w.total) return LS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ParDev P = make_par(params);
+  ProjPtr pw = proj_planes(w.proj, R);
+  ProjCPtr pp = proj_cplanes(w.proj, R);
+  LS_TRY(cudaMemsetAsync(static_cast<char*>(workspace) + w.zero_begin, 0, w.zero_bytes, st));
+  // projection and depth order (as the plain path)
+  if (R > 0) {
+    LS_TRY(launch_project_fwd(n, means, scales, quats, opacities, sh, T, P, pw, nullptr, st));
+    SortScratch ds = sort_scratch_carve(w.depth_scratch, R, 4);
+    LS_TRY(launch_radix_hist(pp.dkey, nullptr, R, 0, 4, ds.hist, st));
+    LS_TRY(launch_radix_scan(ds.hist, 4, st));
+    LS_TRY(launch_onesweep_pass(pp.dkey, nullptr, w.dk_b, w.dv_b, nullptr, R, R, 0, 0, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 1, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_a, w.dv_a, w.dk_b, w.dv_b, nullptr, R, R, 0, 2, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 3, ds, nullptr, status_dev, st));
+    LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n, P, w.rect, w.block_sums, st));
+  }
+  // per-tile features and the proposal
+  LS_TRY(launch_tile_hist(R, pp.rec, pp.foot, pp.dkey, C, P, w.diff, st));
+  LS_TRY(launch_features(w.diff, C, P, w.x16, w.tile_total, w.key_total, st));
+  if (mlp) LS_TRY(launch_mlp_forward(tiles, w.x16, mlp_dev(mlp), w.y, st));
+  LS_TRY(launch_dstar(tiles, mlp ? w.y : nullptr, margin, dstar_in, w.dstar_bits, dstar_out, st));
+  // kept keys: count per warp, scan, emit, sort, blend
+  const int64_t nwarps = R > 0 ? (int64_t)ceil_div(R, DUP_BLOCK) * (DUP_THREADS / 32) : 0;
+  SortScratch ks = sort_scratch_carve(w.kept_scratch, key_capacity > 0 ? key_capacity : 1, kp);
+  SortScratch hs = sort_scratch_carve(w.held_scratch, key_capacity > 0 ? key_capacity : 1, kp);
+  LS_TRY(cudaMemsetAsync(w.k_ranges, 0xFF, 8 * (size_t)tiles, st));
+  LS_TRY(cudaMemsetAsync(w.h_ranges, 0xFF, 8 * (size_t)tiles, st));
+  uint32_t *ek = kp % 2 == 0 ? w.k_keys : w.k_alt_keys, *ev = kp % 2 == 0 ? w.k_vals : w.k_alt_vals;
+  uint32_t *ok = kp % 2 == 0 ? w.k_alt_keys : w.k_keys, *ov = kp % 2 == 0 ? w.k_alt_vals : w.k_vals;
+  if (R > 0) {
+    LS_TRY(launch_enum_keys(false, false, R, w.dv_a, w.dk_a, w.rect, C.tiles_x, w.dstar_bits, w.refuted, w.n_refuted,
+                            w.wc_kept, nullptr, nullptr, nullptr, kp, nullptr, st));
+  }
+  // the per-warp counts are scanned like block sums: nwarps entries
+  LS_TRY(launch_dup_scan(nwarps * DUP_BLOCK, w.wc_kept, key_capacity, w.n_kept, w.n_kept_valid, status_dev, st));
+  if (R > 0 && key_capacity > 0) {
+    LS_TRY(launch_enum_keys(true, false, R, w.dv_a, w.dk_a, w.rect, C.tiles_x, w.dstar_bits, w.refuted, w.n_refuted,
+                            w.wc_kept, w.n_kept_valid, ek, ev, kp, ks.hist, st));
+    ls_status s = tile_sort(ek, ev, ok, ov, w.n_kept_valid, key_capacity, kp, ks, w.k_ranges, tiles, status_dev, st);
+    if (s != LS_OK) return s;
+  } else {
+    LS_TRY(launch_ranges_fixup(w.k_ranges, tiles, st));
+  }
+  TruncArgs ta{};
+  ta.t_thr = t_thr;
+  ta.tile_total = w.tile_total;
+  ta.refuted = w.refuted;
+  ta.n_refuted = w.n_refuted;
+  ta.kept_ranges = reinterpret_cast<const int2*>(w.k_ranges);
+  LS_TRY(launch_blend_trunc(1, pp.rec, C, P, reinterpret_cast<const int2*>(w.k_ranges), w.k_vals, image, t_final,
+                            n_last, ta, st));
+  // held-out keys of refuted tiles (every kernel returns at once when none)
+  uint32_t *hk = kp % 2 == 0 ? w.h_keys : w.h_alt_keys, *hv = kp % 2 == 0 ? w.h_vals : w.h_alt_vals;
+  uint32_t *hok = kp % 2 == 0 ? w.h_alt_keys : w.h_keys, *hov = kp % 2 == 0 ? w.h_alt_vals : w.h_vals;
+  if (R > 0) {
+    LS_TRY(launch_enum_keys(false, true, R, w.dv_a, w.dk_a, w.rect, C.tiles_x, w.dstar_bits, w.refuted, w.n_refuted,
+                            w.wc_held, nullptr, nullptr, nullptr, kp, nullptr, st));
+  }
+  LS_TRY(launch_dup_scan(nwarps * DUP_BLOCK, w.wc_held, key_capacity, w.n_held, w.n_held_valid, status_dev, st));
+  if (R > 0 && key_capacity > 0) {
+    LS_TRY(launch_enum_keys(true, true, R, w.dv_a, w.dk_a, w.rect, C.tiles_x, w.dstar_bits, w.refuted, w.n_refuted,
+                            w.wc_held, w.n_held_valid, hk, hv, kp, hs.hist, st));
+    ls_status s = tile_sort(hk, hv, hok, hov, w.n_held_valid, key_capacity, kp, hs, w.h_ranges, tiles, status_dev, st);
+    if (s != LS_OK) return s;
+  } else {
+    LS_TRY(launch_ranges_fixup(w.h_ranges, tiles, st));
+  }
+  LS_TRY(launch_blend_trunc(2, pp.rec, C, P, reinterpret_cast<const int2*>(w.h_ranges), w.h_vals, image, t_final,
+                            n_last, ta, st));
+  LS_TRY(launch_learned_stats(w.key_total, w.n_kept, w.n_held, w.n_refuted, stats_dev, st));
   return LS_OK;
 }
 

@@ -59,12 +59,26 @@ struct TileJob {
   size_t pix_base;
 };
 
+
 // ---------------------------------------------------------------- forward
-template <int KID, int PPT, bool COUNT>
+// Modes of the per-tile forward:
+//   FWD_PLAIN   one pass over the tile's list;
+//   FWD_TRUNC   the list holds only the keys in front of a proposed depth; a
+//               tile whose pixels are not all settled afterwards (stopped, or
+//               T < t_thr) and that has held-out keys is refuted: it stores
+//               its raw per-pixel state (C without background, T with the
+//               sign bit marking a stopped pixel, n_last) and is flagged;
+//   FWD_RESUME  a refuted tile continues over its held-out list (the rest of
+//               the same front-to-back list) from that state, so the result is
+//               the plain one bit for bit.
+enum { FWD_PLAIN = 0, FWD_TRUNC = 1, FWD_RESUME = 2 };
+
+template <int KID, int PPT, bool COUNT, int MODE>
 __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
                                          const ParDev& P, const TileJob& J, float4* s_a, float4* s_b, float4* s_c,
                                          int B, float* __restrict__ image, float* __restrict__ t_final,
-                                         int32_t* __restrict__ n_last, unsigned long long* stats) {
+                                         int32_t* __restrict__ n_last, unsigned long long* stats,
+                                         const TruncArgs& ta, int tile_gid) {
   const int sx = P.tile_w / PPT;
   const int lr = (int)threadIdx.x / sx, lc = ((int)threadIdx.x % sx) * PPT;
   const int py = J.y0 + lr, px0 = J.x0 + lc;
@@ -72,6 +86,8 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
   float xs[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
   int last[PPT], stop[PPT], comp[PPT];
   unsigned done = 0;
+  int ofs = 0;  // FWD_RESUME: entries of the tile already composited (kept list)
+  if (MODE == FWD_RESUME) ofs = ta.kept_ranges[tile_gid].y - ta.kept_ranges[tile_gid].x;
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
     xs[p] = (float)(px0 + p) + 0.5f;
@@ -79,7 +95,18 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
     C0[p] = C1[p] = C2[p] = 0.f;
     last[p] = 0;
     comp[p] = 0;
-    if (!(px0 + p < J.W && py < J.H)) done |= 1u << p;
+    const bool inside = px0 + p < J.W && py < J.H;
+    if (!inside) done |= 1u << p;
+    if (MODE == FWD_RESUME && inside) {
+      const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p;
+      C0[p] = image[3 * pi];
+      C1[p] = image[3 * pi + 1];
+      C2[p] = image[3 * pi + 2];
+      const float tv = t_final[pi];
+      T[p] = fabsf(tv);
+      if (signbit(tv)) done |= 1u << p;
+      last[p] = n_last[pi];
+    }
   }
   const unsigned all = (1u << PPT) - 1u;
   const int n = J.rg.y - J.rg.x;
@@ -123,17 +150,37 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
           C1[p] += c.y * w;
           C2[p] += c.z * w;
           T[p] = Tn;
-          last[p] = b0 + j + 1;
+          last[p] = ofs + b0 + j + 1;
           if (COUNT) ++comp[p];
         }
         if (done == all) break;
       }
     }
   }
+  bool raw = false;  // FWD_TRUNC: store the state instead of the final colour
+  if (MODE == FWD_TRUNC) {
+    bool settled = true;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) settled = settled && (((done >> p) & 1u) || T[p] < ta.t_thr);
+    const bool all_settled = __syncthreads_and(settled);
+    raw = !all_settled && ta.tile_total[tile_gid] > n;
+    if (raw && threadIdx.x == 0) {
+      ta.refuted[tile_gid] = 1;
+      atomicAdd(ta.n_refuted, 1u);
+    }
+  }
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
     if (px0 + p < J.W && py < J.H) {
       const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p;
+      if (raw) {
+        image[3 * pi] = C0[p];
+        image[3 * pi + 1] = C1[p];
+        image[3 * pi + 2] = C2[p];
+        t_final[pi] = ((done >> p) & 1u) ? -T[p] : T[p];
+        n_last[pi] = last[p];
+        continue;
+      }
       image[3 * pi] = C0[p] + T[p] * P.bg[0];
       image[3 * pi + 1] = C1[p] + T[p] * P.bg[1];
       image[3 * pi + 2] = C2[p] + T[p] * P.bg[2];
@@ -160,13 +207,25 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
         cc += comp[p];
       }
     }
+    int never = 0;  // a pixel that never stopped
+#pragma unroll
+    for (int p = 0; p < PPT; ++p)
+      if (px0 + p < J.W && py < J.H && stop[p] >= n) never = 1;
     atomicMax(&s_emax, emax);
     atomicAdd(&s_npix, npix);
     atomicAdd(&s_contrib, (unsigned long long)cc);
-    __syncthreads();
+    const int any_never = __syncthreads_or(never);
     if (threadIdx.x == 0) {
       atomicAdd(&stats[0], (unsigned long long)s_emax * (unsigned long long)s_npix);
       atomicAdd(&stats[1], s_contrib);
+      if (ta.labels) {
+        // termination depth: depth of the entry at which the tile's last pixel
+        // stopped; +inf when some pixel never stops; 0 for an empty tile
+        float lab = 0.f;
+        if (any_never && n > 0) lab = __int_as_float(0x7F800000);
+        else if (s_npix > 0 && s_emax > 0) lab = rec[3 * (size_t)vals[J.rg.x + s_emax - 1] + 1].w;
+        ta.labels[tile_gid] = lab;
+      }
     }
   }
 }
@@ -176,7 +235,7 @@ __global__ void __launch_bounds__(128) blend_fwd_kernel(const float4* __restrict
                                                         const ParDev P, const int2* __restrict__ ranges,
                                                         const uint32_t* __restrict__ vals, float* __restrict__ image,
                                                         float* __restrict__ t_final, int32_t* __restrict__ n_last,
-                                                        unsigned long long* stats) {
+                                                        unsigned long long* stats, const TruncArgs ta) {
   extern __shared__ float4 smem[];
   const int B = 4 * blockDim.x;
   const int tile = blockIdx.x;
@@ -187,7 +246,31 @@ __global__ void __launch_bounds__(128) blend_fwd_kernel(const float4* __restrict
   J.H = cam.H;
   J.rg = ranges[cam.tile_base + tile];
   J.pix_base = 0;
-  fwd_tile<KID, PPT, COUNT>(rec, vals, P, J, smem, smem + B, smem + 2 * B, B, image, t_final, n_last, stats);
+  fwd_tile<KID, PPT, COUNT, FWD_PLAIN>(rec, vals, P, J, smem, smem + B, smem + 2 * B, B, image, t_final, n_last,
+                                       stats, ta, cam.tile_base + tile);
+}
+
+// Truncated (MODE 1) and resumed (MODE 2) forwards of one camera; a resume
+// CTA whose tile was not refuted returns at once.
+template <int KID, int PPT, int MODE>
+__global__ void __launch_bounds__(128) blend_trunc_kernel(const float4* __restrict__ rec, const CamDev cam,
+                                                          const ParDev P, const int2* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ vals, float* __restrict__ image,
+                                                          float* __restrict__ t_final, int32_t* __restrict__ n_last,
+                                                          const TruncArgs ta) {
+  extern __shared__ float4 smem[];
+  const int B = 4 * blockDim.x;
+  const int tile = blockIdx.x;
+  if (MODE == FWD_RESUME && !ta.refuted[tile]) return;
+  TileJob J;
+  J.x0 = (tile % cam.tiles_x) * P.tile_w;
+  J.y0 = (tile / cam.tiles_x) * P.tile_h;
+  J.W = cam.W;
+  J.H = cam.H;
+  J.rg = ranges[tile];
+  J.pix_base = 0;
+  fwd_tile<KID, PPT, false, MODE>(rec, vals, P, J, smem, smem + B, smem + 2 * B, B, image, t_final, n_last, nullptr, ta,
+                                  tile);
 }
 
 // ---------------------------------------------------------------- backward
@@ -453,7 +536,8 @@ __global__ void __launch_bounds__(128) blend_batch_kernel(const float4* __restri
     J.H = cam.H;
     J.rg = ranges[gt];
     J.pix_base = pix.base[lo];
-    fwd_tile<KID, PPT, false>(rec, vals, P, J, smem, smem + B, smem + 2 * B, B, images, t_final, nullptr, nullptr);
+    fwd_tile<KID, PPT, false, FWD_PLAIN>(rec, vals, P, J, smem, smem + B, smem + 2 * B, B, images, t_final, nullptr,
+                                         nullptr, TruncArgs{}, gt);
   }
 }
 
@@ -464,13 +548,16 @@ static inline int ppt_for(const ParDev& P) { return P.tile_w * P.tile_h >= 256 ?
 
 cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
                              const uint32_t* vals, float* image, float* t_final, int32_t* n_last,
-                             unsigned long long* stats, cudaStream_t st) {
+                             unsigned long long* stats, cudaStream_t st, float* labels) {
+  TruncArgs labels_ta{};
+  labels_ta.labels = labels;
   const int ppt = ppt_for(P);
   const int threads = P.tile_w * P.tile_h / ppt;
   const unsigned grid = (unsigned)(cam.tiles_x * cam.tiles_y);
   const size_t sm = sizeof(float4) * 3 * 4 * threads;
-#define LS_BF3(K, PP, C) \
-  blend_fwd_kernel<K, PP, C><<<grid, threads, sm, st>>>(rec, cam, P, ranges, vals, image, t_final, n_last, stats)
+#define LS_BF3(K, PP, C)                                                                                   \
+  blend_fwd_kernel<K, PP, C><<<grid, threads, sm, st>>>(rec, cam, P, ranges, vals, image, t_final, n_last, stats, \
+                                                        labels_ta)
 #define LS_BF2(K, PP)               \
   do {                              \
     if (stats) LS_BF3(K, PP, true); \
@@ -525,6 +612,38 @@ cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev&
 }  // namespace ls
 
 namespace ls {
+
+cudaError_t launch_blend_trunc(int mode, const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
+                               const uint32_t* vals, float* image, float* t_final, int32_t* n_last,
+                               const TruncArgs& ta, cudaStream_t st) {
+  const int ppt = ppt_for(P);
+  const int threads = P.tile_w * P.tile_h / ppt;
+  const unsigned grid = (unsigned)(cam.tiles_x * cam.tiles_y);
+  const size_t sm = sizeof(float4) * 3 * 4 * threads;
+#define LS_BT3(K, PP, M) \
+  blend_trunc_kernel<K, PP, M><<<grid, threads, sm, st>>>(rec, cam, P, ranges, vals, image, t_final, n_last, ta)
+#define LS_BT2(K, PP)                        \
+  do {                                       \
+    if (mode == 1) LS_BT3(K, PP, FWD_TRUNC); \
+    else LS_BT3(K, PP, FWD_RESUME);          \
+  } while (0)
+#define LS_BT(K)                \
+  do {                          \
+    if (ppt == 4) LS_BT2(K, 4); \
+    else LS_BT2(K, 2);          \
+  } while (0)
+  switch (P.kernel) {
+    case LS_KERNEL_GAUSSIAN: LS_BT(LS_KERNEL_GAUSSIAN); break;
+    case LS_KERNEL_LAPLACIAN: LS_BT(LS_KERNEL_LAPLACIAN); break;
+    case LS_KERNEL_COSINE: LS_BT(LS_KERNEL_COSINE); break;
+    case LS_KERNEL_QUADRATIC: LS_BT(LS_KERNEL_QUADRATIC); break;
+    default: LS_BT(LS_KERNEL_LINEAR); break;
+  }
+#undef LS_BT
+#undef LS_BT2
+#undef LS_BT3
+  return cudaGetLastError();
+}
 
 cudaError_t launch_build_queue(const int32_t* ranges, int total_tiles, uint32_t* queue, unsigned* job_ctr,
                                cudaStream_t st) {

@@ -73,12 +73,48 @@ cudaError_t launch_build_queue(const int32_t* ranges, int total_tiles, uint32_t*
 cudaError_t launch_blend_batch(const float4* rec, const uint32_t* vals, const int32_t* ranges, const CamTable& cams,
                               const BatchPix& pix, const ParDev& P, const uint32_t* queue, int n_jobs,
                               unsigned* job_ctr, float* images, float* t_final, int batch, cudaStream_t st);
+// Extra inputs/outputs of the truncated, resumed and labelled forwards.
+struct TruncArgs {
+  float t_thr;                // a pixel with T < t_thr counts as settled
+  const int32_t* tile_total;  // keys touching each tile before truncation
+  uint8_t* refuted;           // [tiles] set for refuted tiles
+  unsigned* n_refuted;
+  const int2* kept_ranges;    // resume: the kept list of each tile
+  float* labels;              // counting forward: per-tile termination depth
+};
+// labels != nullptr (with stats) also writes each tile's termination depth.
 cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
                              const uint32_t* vals, float* image, float* t_final, int32_t* n_last,
-                             unsigned long long* stats, cudaStream_t st);
+                             unsigned long long* stats, cudaStream_t st, float* labels = nullptr);
+// mode 1: truncated forward over the kept lists; mode 2: resume of refuted tiles
+// over their held-out lists (ranges = held-out ranges).
+cudaError_t launch_blend_trunc(int mode, const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
+                               const uint32_t* vals, float* image, float* t_final, int32_t* n_last,
+                               const TruncArgs& ta, cudaStream_t st);
 cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
                              const uint32_t* vals, const float* t_final, const int32_t* n_last,
                              const float* grad_image, const float* grad_t, float* g2d, cudaStream_t st);
+
+// ---- learned termination (learned.cu)
+struct DepthBins {
+  float edge[31];  // binary32 lower edges of bins 1..31 of log depth
+};
+DepthBins make_depth_bins();
+// Scratch planes of the per-tile histograms (32 float coverage planes and one
+// int count plane of (tiles_x + 1) x (tiles_y + 1)), zeroed by the caller.
+size_t hist_planes_bytes(const CamDev& cam);
+cudaError_t launch_tile_hist(int64_t R, const float4* rec, const float4* foot, const uint32_t* dkey,
+                             const CamDev& cam, const ParDev& P, void* planes, cudaStream_t st);
+cudaError_t launch_features(void* planes, const CamDev& cam, const ParDev& P, void* x, int32_t* tile_total,
+                            unsigned long long* key_total, cudaStream_t st);
+cudaError_t launch_dstar(int ntiles, const float* y, float margin, const float* dstar_in, uint32_t* bits,
+                         float* dstar_out, cudaStream_t st);
+cudaError_t launch_enum_keys(bool emit, bool held, int64_t R, const uint32_t* order, const uint32_t* dkey_sorted,
+                             const uint2* rect_sorted, int tiles_x, const uint32_t* dstar_bits, const uint8_t* refuted,
+                             const unsigned* n_refuted, uint32_t* warp_counts, const int64_t* n_valid, uint32_t* keys,
+                             uint32_t* vals, int key_passes, uint32_t* tile_hist, cudaStream_t st);
+cudaError_t launch_learned_stats(const unsigned long long* key_total, const int64_t* n_kept, const int64_t* n_held,
+                                 const unsigned* n_refuted, int64_t* stats, cudaStream_t st);
 
 // ---- termination MLP (mlp.cu)
 struct MlpDev {

@@ -16,7 +16,7 @@ import numpy as np
 import torch
 
 from . import _native as N
-from .raster import _p, _stream
+from .raster import Rasterizer, RenderParams, Splats, _p, _stream, cam_struct, tiles_of
 
 NPARAM = 7361
 IN, HID, FEATURES = 48, 64, 35
@@ -108,3 +108,97 @@ class TerminationMLP:
         mlp = TerminationMLP(d["params"], device=device)
         mlp.meta = {k: d[k] for k in d.files if k != "params"}
         return mlp
+
+
+# ---------------------------------------------------------------------------
+# truncated render
+# ---------------------------------------------------------------------------
+LOG_KEEP_ALL = math.log(64.0)  # target of tiles in which some pixel never stops
+
+
+class LearnedRenderer:
+    """Forward render of one camera with learned (or given) per-tile
+    termination depths; exact fallback for refuted tiles."""
+
+    def __init__(self, splats: Splats, cam, params: RenderParams | None = None, device="cuda", margin_keys=1.25):
+        self.splats = splats
+        self.cam = cam
+        self.params = params or RenderParams()
+        self.params.sh_degree = splats.sh_degree
+        self.device = torch.device(device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.stats = torch.zeros(4, dtype=torch.int64, device=self.device)
+        H, W = cam["height"], cam["width"]
+        self.image = torch.empty((H, W, 3), dtype=torch.float32, device=self.device)
+        self.T = torch.empty((H, W), dtype=torch.float32, device=self.device)
+        self.n_last = torch.empty((H, W), dtype=torch.int32, device=self.device)
+        self.tiles = tiles_of(cam, self.params)
+        self.dstar = torch.empty(self.tiles, dtype=torch.float32, device=self.device)
+        self._c = cam_struct(cam)
+        self._pc = self.params.c()
+        rz = Rasterizer(self.params, device=self.device)
+        _, tc = rz.project(splats, [cam], counts=True)
+        self.capacity = int(tc.sum(dtype=torch.int64).item() * margin_keys) + 1024
+        wsb = N.lib().ls_render_learned_workspace(splats.n, ctypes.byref(self._c), ctypes.byref(self._pc),
+                                                  self.capacity)
+        self._ws = torch.empty(wsb + 256, dtype=torch.uint8, device=self.device)
+        self._ws_ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        self._ws_bytes = wsb
+
+    def render(self, mlp: TerminationMLP | None = None, margin=0.0, dstar_in=None, t_thr=None):
+        """mlp, or per-tile depths dstar_in [tiles]; t_thr None = exact."""
+        sp = self.splats
+        thr = self.params.t_min if t_thr is None else t_thr
+        net = ctypes.byref(mlp.c()) if mlp is not None else None
+        if mlp is None and dstar_in is None:
+            raise ValueError("an MLP or per-tile depths")
+        N.check(N.lib().ls_render_learned(sp.n, _p(sp.means), _p(sp.scales), _p(sp.quats), _p(sp.opac), _p(sp.sh),
+                                          ctypes.byref(self._c), ctypes.byref(self._pc), net, float(margin),
+                                          _p(dstar_in), float(thr), self.capacity, _p(self.image), _p(self.T),
+                                          _p(self.n_last), _p(self.dstar), _p(self.stats),
+                                          ctypes.c_void_p(self._ws_ptr), self._ws_bytes, _p(self.status), _stream()),
+                "ls_render_learned")
+        return self.image, self.T
+
+    def counters(self):
+        """(keys before truncation, kept, held-out sorted, refuted tiles)."""
+        return tuple(int(v) for v in self.stats.cpu().tolist())
+
+    def check(self):
+        s = int(self.status.item())
+        if s != 0:
+            raise N.LsError(s, "ls_render_learned")
+
+
+# ---------------------------------------------------------------------------
+# training data and training
+# ---------------------------------------------------------------------------
+def tile_examples(rz: Rasterizer, splats: Splats, cam):
+    """(features [m, 48] fp16, targets [m] fp32) of the non-empty tiles of one
+    plain render: the target is the log of the depth at which the tile's last
+    pixel stopped, LOG_KEEP_ALL when some pixel never stops.  A rasterizer
+    whose t_min is a threshold t_thr gives the targets of the truncated render
+    at t_thr: a pixel stops at the first entry that would take T below it."""
+    image, T, state = rz.forward(splats, cam)
+    nt = tiles_of(cam, rz.params)
+    labels = torch.empty(nt, dtype=torch.float32, device=rz.device)
+    rz.render_stats(state["proj"], splats.n, cam, state["ranges"], state["vals"], labels=labels)
+    x, total = rz.tile_features(state["proj"], splats.n, cam)
+    keep = total > 0
+    y = torch.where(torch.isinf(labels), torch.full_like(labels, LOG_KEEP_ALL),
+                    torch.log(torch.clamp(labels, min=1e-3)))
+    return x[keep], y[keep]
+
+
+def train(mlp: TerminationMLP, x, y, steps=2000, batch=65536, lr=1e-3, under_weight=4.0, seed=0, log_every=0):
+    """Adam on shuffled minibatches of (x, y), all on the GPU."""
+    g = torch.Generator(device=x.device)
+    g.manual_seed(seed)
+    m = x.shape[0]
+    losses = []
+    for s in range(steps):
+        idx = torch.randint(0, m, (min(batch, m),), device=x.device, generator=g)
+        loss = mlp.train_step(x[idx].contiguous(), y[idx].contiguous(), lr=lr, under_weight=under_weight)
+        if log_every and (s % log_every == 0 or s == steps - 1):
+            losses.append((s, float(loss.item())))
+    return losses

@@ -218,8 +218,9 @@ class Rasterizer:
                 "ls_render_fwd")
         return image, T, n_last
 
-    def render_stats(self, proj, R, cam, ranges, vals):
-        """Forward blend that also returns (evaluated pairs, composited pairs)."""
+    def render_stats(self, proj, R, cam, ranges, vals, labels=None):
+        """Forward blend that also returns (evaluated pairs, composited pairs);
+        with `labels` (float [tiles]) also each tile's termination depth."""
         P = self.params
         H, W = cam["height"], cam["width"]
         image = torch.empty((H, W, 3), dtype=torch.float32, device=self.device)
@@ -227,10 +228,24 @@ class Rasterizer:
         n_last = torch.empty((H, W), dtype=torch.int32, device=self.device)
         stats = torch.zeros(2, dtype=torch.int64, device=self.device)
         N.check(N.lib().ls_render_stats(_p(proj), R, ctypes.byref(cam_struct(cam)), ctypes.byref(P.c()), _p(ranges),
-                                        _p(vals), _p(image), _p(T), _p(n_last), _p(stats), _p(self.status),
-                                        _stream()), "ls_render_stats")
+                                        _p(vals), _p(image), _p(T), _p(n_last), _p(stats), _p(labels),
+                                        _p(self.status), _stream()), "ls_render_stats")
         s = stats.cpu().tolist()
         return image, T, n_last, int(s[0]), int(s[1])
+
+    def tile_features(self, proj, R, cam):
+        """MLP inputs [tiles, 48] (fp16) and keys per tile [tiles] (int32)."""
+        P = self.params
+        nt = tiles_of(cam, P)
+        x = torch.empty((nt, 48), dtype=torch.float16, device=self.device)
+        total = torch.empty(nt, dtype=torch.int32, device=self.device)
+        c, pc = cam_struct(cam), P.c()
+        wsb = N.lib().ls_tile_features_workspace(ctypes.byref(c), ctypes.byref(pc))
+        ws = self._buf("feat_ws", wsb + 256)
+        ws_ptr = (ws.data_ptr() + 255) // 256 * 256
+        N.check(N.lib().ls_tile_features(_p(proj), R, ctypes.byref(c), ctypes.byref(pc), _p(x), _p(total),
+                                         ctypes.c_void_p(ws_ptr), wsb, _stream()), "ls_tile_features")
+        return x, total
 
     def blend_bwd(self, proj, R, cam, ranges, vals, T, n_last, grad_image, grad_T, g2d):
         """a5 alone: accumulates into g2d [R, 12] (zero it first)."""

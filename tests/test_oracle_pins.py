@@ -403,3 +403,51 @@ def test_view_direction_convention():
     assert vis[0]
     expect = 0.5 - float(np.float32(c)) * math.sqrt(3 / (4 * math.pi))
     assert proj[0, oracle.P_R:oracle.P_BL + 1] == pytest.approx([expect] * 3, abs=1e-12)
+
+
+def test_tile_termination_labels_closed_form():
+    """One 16x16 tile covered by two large primitives (depths 2 and 3): with
+    T_min = 0.9 every pixel stops at the first entry, so the tile's label is
+    2.0; with T_min = 0 no pixel stops, so it is +inf; an empty view gives 0."""
+    s = scenes.Scene(np.array([[0, 0, 2.0], [0, 0, 3.0]], np.float32), np.full((2, 3), 1.0, np.float32),
+                     np.array([[1, 0, 0, 0]] * 2, np.float32), np.array([0.9, 0.9], np.float32),
+                     np.zeros((2, 1, 3), np.float32), 0)
+    cam = scenes.camera(np.eye(4), 20.0, 20.0, 8.0, 8.0, 16, 16)
+    out = oracle.render_scene(s, cam, dict(t_min=0.9))
+    assert out["labels"].tolist() == [pytest.approx(2.0)]
+    out = oracle.render_scene(s, cam, dict(t_min=0.0))
+    assert out["labels"].tolist() == [np.inf]
+    far = s.subset([0])
+    far.means = np.array([[50.0, 0, 2.0]], np.float32)  # off screen
+    assert oracle.render_scene(far, cam)["labels"].tolist() == [0.0]
+
+
+def test_tile_depth_hist_brute_force():
+    """Counts of random footprints against a direct count with numpy; the
+    coverage is cumulative over bins and conserves each record's weight:
+    summed over tiles, the last bin equals sum_r w_r (tiles in r's box)."""
+    W, H, TW, TH = 160, 96, 16, 16
+    rec = scenes.random_records(500, W, H, seed=12)
+    foot = np.concatenate([rec["mean2d"], rec["ext"]], 1)
+    dkey = oracle.depth_keys(rec)
+    proj = oracle.records_to_proj(rec)
+    counts, cov = oracle.tile_depth_hist(foot, dkey, proj, W, H, TW, TH)
+    exp = np.zeros_like(counts)
+    tx_n = (W + TW - 1) // TW
+    total_w = 0.0
+    for r in range(500):
+        if not rec["visible"][r]:
+            continue
+        rc = oracle.rect(*foot[r].astype(np.float64).tolist(), W, H, True)
+        if rc is None:
+            continue
+        n_t = (rc[1] // TW - rc[0] // TW + 1) * (rc[3] // TH - rc[2] // TH + 1)
+        for ty in range(rc[2] // TH, rc[3] // TH + 1):
+            for tx in range(rc[0] // TW, rc[1] // TW + 1):
+                exp[ty * tx_n + tx] += 1
+        l00, l01, l11 = (float(v) for v in rec["chol"][r])
+        ellipse = math.pi * float(rec["rho2"][r]) / (l00 * l11)   # det A = (l00 l11)^2
+        total_w += n_t * float(rec["opac"][r]) / 3.0 * min(1.0, ellipse / (n_t * TW * TH))
+    assert np.array_equal(counts, exp) and counts.sum() > 0
+    assert (np.diff(cov, axis=1) >= 0).all()
+    assert cov[:, -1].sum() == pytest.approx(total_w, rel=1e-9)
