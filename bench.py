@@ -258,6 +258,132 @@ def bench_batched(dev, reps=10):
 
 
 # --------------------------------------------------------------------------
+# kernel family: the same frame with the Gaussian kernel as the speed control
+# --------------------------------------------------------------------------
+def time_frame(sp, cam, P, dev, steps=20, warmup=3):
+    """Median forward (project + duplicate/sort + blend) and backward (blend
+    adjoint + projection adjoint) ms of one camera, and the frame's units."""
+    import torch
+    from paper_2411_12440_gb300 import raster, scenes
+    rz = raster.Rasterizer(P, device=dev)
+    R = sp.n
+    H, W = cam["height"], cam["width"]
+    w, v = scenes.loss_weights(H, W, seed=7)
+    gimg, gT = torch.from_numpy(w).to(dev), torch.from_numpy(v).to(dev)
+    g2d = torch.empty((R, 12), dtype=torch.float32, device=dev)
+    proj, tc = rz.project(sp, [cam], counts=True)
+    rz.ensure_capacity(tc)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for i in range(warmup + steps):
+        e = evs[i - warmup] if i >= warmup else None
+        if e:
+            e[0].record()
+        proj, _ = rz.project(sp, [cam], counts=False)
+        keys, vals, n_keys, ranges = rz.duplicate_sort(proj, R, [cam])
+        image, T, n_last = rz.render_fwd(proj, R, cam, ranges, vals)
+        if e:
+            e[1].record()
+        g2d.zero_()
+        rz.blend_bwd(proj, R, cam, ranges, vals, T, n_last, gimg, gT, g2d)
+        rz.project_bwd(sp, [cam], proj, g2d)
+        if e:
+            e[2].record()
+    torch.cuda.synchronize(dev)
+    rz.check_status("kernel family")
+    fwd = statistics.median(e[0].elapsed_time(e[1]) for e in evs)
+    bwd = statistics.median(e[1].elapsed_time(e[2]) for e in evs)
+    _, _, _, n_eval, n_contrib = rz.render_stats(proj, R, cam, ranges, vals)
+    return {"fwd_ms": fwd, "bwd_ms": bwd, "tile_keys": int(n_keys.item()), "pairs_evaluated": n_eval,
+            "pairs_composited": n_contrib}
+
+
+def bench_kernel_family(sp, cam, antialias, dev):
+    """Linear kernel (lambda 2.5) against the Gaussian (lambda 1, support at
+    3 sigma or alpha_min) on the same primitives: the paper's speed claim."""
+    import dataclasses
+    from paper_2411_12440_gb300 import raster
+    base = raster.RenderParams(sh_degree=3, antialias=antialias)
+    out = {"linear": time_frame(sp, cam, dataclasses.replace(base, kernel=0, lam=2.5), dev),
+           "gaussian": time_frame(sp, cam, dataclasses.replace(base, kernel=1, lam=1.0), dev)}
+    out["gaussian_over_linear_fwd"] = out["gaussian"]["fwd_ms"] / out["linear"]["fwd_ms"]
+    out["gaussian_over_linear_bwd"] = out["gaussian"]["bwd_ms"] / out["linear"]["bwd_ms"]
+    return out
+
+
+# --------------------------------------------------------------------------
+# learned termination: 5M primitives, one 1920x1080 view on the ring
+# --------------------------------------------------------------------------
+def bench_learned(dev, reps=20):
+    """Plain forward frame against the learned-termination frame (trained
+    network plus calibrated margin, lossy threshold t_thr) and the same
+    truncated pipeline without the network: every key kept, and one global
+    depth tuned on the training views.  PSNR against the plain frame."""
+    import math
+    import torch
+    from paper_2411_12440_gb300 import raster, scenes
+    from paper_2411_12440_gb300.learned import LearnedRenderer, TerminationMLP
+    net = TerminationMLP.load(os.path.join(ROOT, "paper_2411_12440_gb300", "data", "termination_mlp.npz"),
+                              device=dev)
+    margin, t_thr = float(net.meta["margin"]), float(net.meta["t_thr"])
+    const = float(net.meta["const_dstar"]) if "const_dstar" in net.meta else None
+    scene, cams, _ = scenes.make_workload("learned_5m_1080p")
+    cam = cams[0]
+    sp = raster.Splats.from_scene(scene, device=dev)
+    del scene
+    P = raster.RenderParams(sh_degree=3)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    def psnr(img, ref):
+        mse = float(((img - ref) ** 2).mean().item())
+        return math.inf if mse == 0.0 else -10.0 * math.log10(mse)
+
+    out = {"workload": "learned_5m_1080p", "prims": sp.n, "width": cam["width"], "height": cam["height"],
+           "t_thr": t_thr, "margin": margin, "const_dstar": const}
+    rz = raster.Rasterizer(P, device=dev)
+    img0, _, st0 = rz.forward(sp, cam)
+    img0 = img0.clone()
+    out["plain"] = {"ms": timed(lambda: rz.forward(sp, cam, sync_capacity=False)),
+                    "keys_sorted": int(st0["n_keys"].item())}
+    rz.check_status("plain")
+    rzt = raster.Rasterizer(raster.RenderParams(sh_degree=3, t_min=t_thr), device=dev)
+    rzt.forward(sp, cam)
+    out["plain_t_thr"] = {"ms": timed(lambda: rzt.forward(sp, cam, sync_capacity=False))}
+    out["plain_t_thr"]["psnr_db"] = psnr(rzt.forward(sp, cam)[0], img0)
+    rzt.check_status("plain at t_thr")
+    del rz, rzt
+    torch.cuda.empty_cache()
+    lr = LearnedRenderer(sp, cam, P, device=dev)
+    modes = {"mlp": dict(mlp=net, margin=margin),
+             "keep_all": dict(dstar_in=torch.full((lr.tiles,), math.inf, device=dev))}
+    if const is not None:
+        modes["const"] = dict(dstar_in=torch.full((lr.tiles,), const, device=dev))
+    for name, kw in modes.items():
+        ms = timed(lambda: lr.render(t_thr=t_thr, **kw))
+        lr.check()
+        total, kept, held, refuted = lr.counters()
+        out[name] = {"ms": ms, "keys_sorted": kept + held, "keys_kept": kept, "keys_held_sorted": held,
+                     "tiles_refuted": refuted, "psnr_db": psnr(lr.image, img0),
+                     "max_abs_err": float((lr.image - img0).abs().max().item())}
+    out["tiles"] = lr.tiles
+    out["speedup_vs_plain"] = out["plain"]["ms"] / out["mlp"]["ms"]
+    out["speedup_vs_keep_all"] = out["keep_all"]["ms"] / out["mlp"]["ms"]
+    if const is not None:
+        out["speedup_vs_const"] = out["const"]["ms"] / out["mlp"]["ms"]
+    return out
+
+
+# --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
 def main():
@@ -271,6 +397,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-camera batched measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-termination measurement")
+    ap.add_argument("--no-family", action="store_true", help="skip the linear-vs-Gaussian measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -326,6 +454,8 @@ def main():
     n_vis = int((dk != -1).sum().item())
     keys, vals, n_keys, ranges = rz.duplicate_sort(proj, R, [cam])
     _, _, _, n_eval, n_contrib = rz.render_stats(proj, R, cam, ranges, vals)
+    K_box = K
+    K = int(n_keys.item())
     del proj, tc
     for _ in range(args.warmup):
         step()
@@ -449,7 +579,8 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single"},
             "fwd_fps": ws * 1e3 / fwd_ms, "fwd_ms": fwd_ms,
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-            "units": {"tile_keys": K, "visible": n_vis, "pairs_evaluated": n_eval, "pairs_composited": n_contrib},
+            "units": {"tile_keys": K, "box_tile_keys": K_box, "visible": n_vis, "pairs_evaluated": n_eval,
+                      "pairs_composited": n_contrib},
             "roofline": roof, "clocks": clocks.summary(), "e2e": e2e,
             # per step: project 1; duplicate_sort 11 + kp (depth hist, scan, 4 passes, count, scan, emit,
             # scan, kp tile passes, ranges); blend fwd, blend bwd, project bwd 1 each
@@ -457,6 +588,10 @@ def main():
 
     if not args.no_batch and args.prims is None:
         line["batched"] = bench_batched(dev)
+    if not args.no_family and args.prims is None:
+        line["kernel_family"] = bench_kernel_family(sp, cam, int(extra["antialias"]), dev)
+    if not args.no_learned and args.prims is None:
+        line["learned"] = bench_learned(dev)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         ncores = os.cpu_count() or 1
         est, sample, spent = oracle_frame_estimate(scene, cam, dict(sh_degree=3, antialias=int(extra["antialias"])),

@@ -111,9 +111,14 @@ ls_status ls_project(int32_t n, const float* means, const float* scales, const f
 /* Workspace of ls_duplicate_sort in bytes. */
 size_t ls_duplicate_sort_workspace(int64_t n_records, int64_t key_capacity, int32_t total_tiles);
 
-/* a2+a3: duplication of every visible record into the tiles its support box
- * touches, and a stable radix sort into front-to-back order per tile
- * (compositing order of Sec. 3.1 Eq. 6, kept "without alteration", Sec. 3.2).
+/* a2+a3: duplication of every visible record into the tiles of its support
+ * box that its support ellipse D^2 <= rho^2 reaches (minimum of D^2 over the
+ * rectangle of the tile's pixel centres, tested in binary32 with a 2 % margin,
+ * so every pair the blend can composite is listed), and a stable radix sort
+ * into front-to-back order per tile (compositing order of Sec. 3.1 Eq. 6,
+ * kept "without alteration", Sec. 3.2).  K is at most the sum of the
+ * tile_counts of ls_project (the box tiles), which therefore bounds the
+ * capacity a caller needs.
  * Tile ids are global over the cameras: camera c's tiles follow those of
  * cameras 0..c-1, row-major within a camera.  Output, for K keys:
  *   keys [K] tile ids ascending; vals [K] record ids, ordered inside a tile by

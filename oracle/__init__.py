@@ -52,6 +52,7 @@ def lib():
         L.lso_render_bwd.restype = ctypes.c_int
         L.lso_project_bwd.restype = ctypes.c_int
         L.lso_dupsort_f32.restype = ctypes.c_longlong
+        L.lso_touch_pairs.restype = ctypes.c_longlong
         L.lso_kernel_f.restype = ctypes.c_double
         L.lso_kernel_f.argtypes = [ctypes.c_int, ctypes.c_double]
         L.lso_kernel_support.restype = ctypes.c_double
@@ -223,6 +224,25 @@ def dupsort_f32(foot, dkey, width, height, tile_w, tile_h, cap=None):
     if K < 0:
         raise RuntimeError("oracle dupsort capacity exceeded")
     return keys[:K].copy(), vals[:K].copy(), ranges.reshape(-1, 2)
+
+
+def touch_pairs(foot, dkey, conic, rho2, width, height, tile_w, tile_h, shrink=1.0):
+    """(tile, record) pairs whose tile holds a pixel centre inside the
+    record's support ellipse scaled by `shrink` (FP64 brute force), within
+    its binary32 support box; sorted by (tile, record)."""
+    R = foot.shape[0]
+    foot = np.ascontiguousarray(foot, dtype=np.float32)
+    dkey = np.ascontiguousarray(dkey, dtype=np.uint32)
+    conic = np.ascontiguousarray(conic, dtype=np.float64)
+    rho2 = np.ascontiguousarray(rho2, dtype=np.float64)
+    args = (ctypes.c_longlong(R), _p(foot), _p(dkey), _p(conic), _p(rho2), ctypes.c_int(width), ctypes.c_int(height),
+            ctypes.c_int(tile_w), ctypes.c_int(tile_h), ctypes.c_double(shrink))
+    n = lib().lso_touch_pairs(*args, ctypes.c_longlong(0), None, None)
+    t = np.zeros(max(n, 1), dtype=np.uint32)
+    r = np.zeros(max(n, 1), dtype=np.uint32)
+    lib().lso_touch_pairs(*args, ctypes.c_longlong(n), _p(t), _p(r))
+    order = np.lexsort((r[:n], t[:n]))
+    return t[:n][order], r[:n][order]
 
 
 def rect(mx, my, ex, ey, width, height, f32):

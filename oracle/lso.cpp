@@ -539,6 +539,44 @@ long long lso_dupsort_f32(long long R, const float* foot, const uint32_t* dkey, 
   return K;
 }
 
+// (tile, record) pairs that every tile list must hold: tiles of a record's
+// binary32 support box (the rule above) with at least one pixel centre
+// (px + 1/2, py + 1/2) inside the shrunken support ellipse
+// q = a dx^2 + 2 b dx dy + c dy^2 <= shrink * rho^2 (FP64, brute force over
+// the tile's pixels).  conic [R][3] = a b c, rho2 [R].  A tile list that
+// holds these pairs lets the blend composite every pair whose alpha reaches
+// alpha_min (compact support of the kernel, Sec. 3.2 Eq. 11-12); pairs on
+// the boundary (shrink < 1) are left to binary32 rounding.  Returns the count
+// (pairs written while it is below cap).
+long long lso_touch_pairs(long long R, const float* foot, const uint32_t* dkey, const double* conic,
+                          const double* rho2, int W, int H, int TW, int TH, double shrink, long long cap,
+                          uint32_t* tile_out, uint32_t* rec_out) {
+  int tx_n = (W + TW - 1) / TW;
+  long long n = 0;
+  for (long long r = 0; r < R; ++r) {
+    if (dkey[r] == 0xFFFFFFFFu) continue;
+    Rect rc = rect_f32(foot[4 * r], foot[4 * r + 1], foot[4 * r + 2], foot[4 * r + 3], W, H);
+    if (rc.empty) continue;
+    const double a = conic[3 * r], b = conic[3 * r + 1], c = conic[3 * r + 2], lim = shrink * rho2[r];
+    for (int ty = rc.y0 / TH; ty <= rc.y1 / TH; ++ty)
+      for (int tx = rc.x0 / TW; tx <= rc.x1 / TW; ++tx) {
+        bool hit = false;
+        for (int py = std::max(ty * TH, rc.y0); py <= std::min(ty * TH + TH - 1, rc.y1) && !hit; ++py)
+          for (int px = std::max(tx * TW, rc.x0); px <= std::min(tx * TW + TW - 1, rc.x1) && !hit; ++px) {
+            const double dx = px + 0.5 - foot[4 * r], dy = py + 0.5 - foot[4 * r + 1];
+            hit = a * dx * dx + 2.0 * b * dx * dy + c * dy * dy <= lim;
+          }
+        if (!hit) continue;
+        if (n < cap) {
+          tile_out[n] = (uint32_t)(ty * tx_n + tx);
+          rec_out[n] = (uint32_t)r;
+        }
+        ++n;
+      }
+  }
+  return n;
+}
+
 // Per-tile inputs of the termination network from binary32 footprints foot
 // [R][4] and depth bits dkey, with each record's opacity, squared support
 // radius and conic taken from proj [R][NP]: counts [tiles] = records whose

@@ -45,7 +45,9 @@ class BatchRenderer:
 
     # ---------------------------------------------------------------- planning
     def count_keys(self):
-        """Exact number of tile keys of the current scene (one host read)."""
+        """Upper bound on the tile keys of the current scene: the support-box
+        tiles of every record (one host read); the keys actually made are the
+        box tiles the support ellipses reach."""
         from .raster import Rasterizer
         rz = Rasterizer(self.params, device=self.device)
         _, tc = rz.project(self.splats, self.cams, counts=True)

@@ -112,7 +112,7 @@ ProjCPtr proj_cplanes(const void* proj, int64_t R) {
 struct DupWs {
   uint32_t *dk_a, *dv_a, *dk_b, *dv_b;  // depth sort ping-pong [R]
   uint2* rect;                          // [R]
-  uint32_t* block_sums;                 // [nb]
+  uint32_t* warp_counts;                // [enum warps]
   int64_t* n_valid;
   uint32_t *k_alt, *v_alt;              // tile sort ping-pong [cap]
   void* depth_scratch;
@@ -135,7 +135,7 @@ DupWs dup_layout(char* base, int64_t R, int64_t cap, int key_passes) {
   w.dk_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
   w.dv_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
   w.rect = reinterpret_cast<uint2*>(take(8 * Rz));
-  w.block_sums = reinterpret_cast<uint32_t*>(take(4 * ((Rz + DUP_BLOCK - 1) / DUP_BLOCK)));
+  w.warp_counts = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
   w.n_valid = reinterpret_cast<int64_t*>(take(8));
   w.k_alt = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.v_alt = reinterpret_cast<uint32_t*>(take(4 * Cz));
@@ -228,9 +228,25 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
     LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 1, ds, nullptr, status_dev, st));
     LS_TRY(launch_onesweep_pass(w.dk_a, w.dv_a, w.dk_b, w.dv_b, nullptr, R, R, 0, 2, ds, nullptr, status_dev, st));
     LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 3, ds, nullptr, status_dev, st));
-    LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n_per_cam, P, w.rect, w.block_sums, st));
+    LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n_per_cam, P, w.rect, st));
   }
-  LS_TRY(launch_dup_scan(R, w.block_sums, key_capacity, n_keys_dev, w.n_valid, status_dev, st));
+  // keys of the tiles each support ellipse reaches: count per warp, scan
+  // (total K and the capacity check), then write in depth order
+  EnumArgs ea{};
+  ea.R = R;
+  ea.order = w.dv_a;
+  ea.dkey_sorted = w.dk_a;
+  ea.rect_sorted = w.rect;
+  ea.rec = pp.rec;
+  ea.cams = T;
+  ea.n_per_cam = n_per_cam;
+  ea.tile_w = P.tile_w;
+  ea.tile_h = P.tile_h;
+  ea.warp_counts = w.warp_counts;
+  ea.n_valid = w.n_valid;
+  ea.key_passes = kp;
+  LS_TRY(launch_enum_keys(false, ENUM_ALL, ea, st));
+  LS_TRY(launch_dup_scan(enum_warps(R), w.warp_counts, key_capacity, n_keys_dev, w.n_valid, status_dev, st));
   // emission goes to the buffer that makes the last tile-sort pass end in
   // the caller's keys/vals
   uint32_t* ek = (kp % 2 == 0) ? keys : w.k_alt;
@@ -241,7 +257,10 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
   // ranges: accumulated by the last tile pass as (min start, ~max end)
   LS_TRY(cudaMemsetAsync(tile_ranges, 0xFF, sizeof(int32_t) * 2 * (size_t)total_tiles, st));
   if (R > 0 && key_capacity > 0) {
-    LS_TRY(launch_dup_emit(R, w.dv_a, w.rect, w.block_sums, T, n_per_cam, w.n_valid, ek, ev, kp, ts.hist, st));
+    ea.keys = ek;
+    ea.vals = ev;
+    ea.tile_hist = ts.hist;
+    LS_TRY(launch_enum_keys(true, ENUM_ALL, ea, st));
     LS_TRY(launch_radix_scan(ts.hist, kp, st));
     for (int p = 0; p < kp; ++p) {
       LS_TRY(launch_onesweep_pass(ek, ev, ok, ov, w.n_valid, 0, key_capacity, 0, p, ts,
@@ -472,17 +491,18 @@ struct LearnedWs {
   char* proj;
   uint32_t *dk_a, *dv_a, *dk_b, *dv_b;
   uint2* rect;
-  uint32_t* block_sums;
   int* diff;
   int32_t* tile_total;
   void* x16;
   float* y;
   uint32_t* dstar_bits;
   uint8_t* refuted;
+  uint8_t* has_held;
   uint32_t *wc_kept, *wc_held;
   uint32_t *k_keys, *k_vals, *k_alt_keys, *k_alt_vals;
   uint32_t *h_keys, *h_vals, *h_alt_keys, *h_alt_vals;
   int32_t *k_ranges, *h_ranges;
+  int* sat;
   int64_t *n_kept, *n_kept_valid, *n_held, *n_held_valid;
   unsigned* n_refuted;
   unsigned long long* key_total;
@@ -500,20 +520,19 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
     return p;
   };
   const size_t Rz = (size_t)(R > 0 ? R : 1), Cz = (size_t)(cap > 0 ? cap : 1);
-  const size_t tiles = (size_t)tiles_x * tiles_y, nb = (Rz + DUP_BLOCK - 1) / DUP_BLOCK;
+  const size_t tiles = (size_t)tiles_x * tiles_y;
   w.proj = take(ls_proj_bytes((int64_t)Rz));
   w.dk_a = reinterpret_cast<uint32_t*>(take(4 * Rz));
   w.dv_a = reinterpret_cast<uint32_t*>(take(4 * Rz));
   w.dk_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
   w.dv_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
   w.rect = reinterpret_cast<uint2*>(take(8 * Rz));
-  w.block_sums = reinterpret_cast<uint32_t*>(take(4 * nb));
   w.tile_total = reinterpret_cast<int32_t*>(take(4 * tiles));
   w.x16 = take(2 * LS_MLP_IN * tiles);
   w.y = reinterpret_cast<float*>(take(4 * tiles));
   w.dstar_bits = reinterpret_cast<uint32_t*>(take(4 * tiles));
-  w.wc_kept = reinterpret_cast<uint32_t*>(take(4 * nb * (DUP_THREADS / 32)));
-  w.wc_held = reinterpret_cast<uint32_t*>(take(4 * nb * (DUP_THREADS / 32)));
+  w.wc_kept = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
+  w.wc_held = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
   w.k_keys = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.k_vals = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.k_alt_keys = reinterpret_cast<uint32_t*>(take(4 * Cz));
@@ -522,12 +541,14 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
   w.h_vals = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.h_alt_keys = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.h_alt_vals = reinterpret_cast<uint32_t*>(take(4 * Cz));
+  w.sat = reinterpret_cast<int*>(take(4 * (size_t)(tiles_x + 1) * (tiles_y + 1)));
   w.k_ranges = reinterpret_cast<int32_t*>(take(8 * tiles));
   w.h_ranges = reinterpret_cast<int32_t*>(take(8 * tiles));
   // cleared before every call
   w.zero_begin = off;
   w.diff = reinterpret_cast<int*>(take(4 * 33 * (size_t)(tiles_x + 1) * (tiles_y + 1)));
   w.refuted = reinterpret_cast<uint8_t*>(take(tiles));
+  w.has_held = reinterpret_cast<uint8_t*>(take(tiles));
   w.n_kept = reinterpret_cast<int64_t*>(take(8));
   w.n_kept_valid = reinterpret_cast<int64_t*>(take(8));
   w.n_held = reinterpret_cast<int64_t*>(take(8));
@@ -626,30 +647,47 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
     LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 1, ds, nullptr, status_dev, st));
     LS_TRY(launch_onesweep_pass(w.dk_a, w.dv_a, w.dk_b, w.dv_b, nullptr, R, R, 0, 2, ds, nullptr, status_dev, st));
     LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 3, ds, nullptr, status_dev, st));
-    LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n, P, w.rect, w.block_sums, st));
+    LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n, P, w.rect, st));
   }
   // per-tile features and the proposal
   LS_TRY(launch_tile_hist(R, pp.rec, pp.foot, pp.dkey, C, P, w.diff, st));
-  LS_TRY(launch_features(w.diff, C, P, w.x16, w.tile_total, w.key_total, st));
+  LS_TRY(launch_features(w.diff, C, P, w.x16, w.tile_total, nullptr, st));
   if (mlp) LS_TRY(launch_mlp_forward(tiles, w.x16, mlp_dev(mlp), w.y, st));
   LS_TRY(launch_dstar(tiles, mlp ? w.y : nullptr, margin, dstar_in, w.dstar_bits, dstar_out, st));
-  // kept keys: count per warp, scan, emit, sort, blend
-  const int64_t nwarps = R > 0 ? (int64_t)ceil_div(R, DUP_BLOCK) * (DUP_THREADS / 32) : 0;
+  // kept keys: count per warp (and every key the ellipses reach), scan,
+  // emit, sort, blend
   SortScratch ks = sort_scratch_carve(w.kept_scratch, key_capacity > 0 ? key_capacity : 1, kp);
   SortScratch hs = sort_scratch_carve(w.held_scratch, key_capacity > 0 ? key_capacity : 1, kp);
   LS_TRY(cudaMemsetAsync(w.k_ranges, 0xFF, 8 * (size_t)tiles, st));
   LS_TRY(cudaMemsetAsync(w.h_ranges, 0xFF, 8 * (size_t)tiles, st));
   uint32_t *ek = kp % 2 == 0 ? w.k_keys : w.k_alt_keys, *ev = kp % 2 == 0 ? w.k_vals : w.k_alt_vals;
   uint32_t *ok = kp % 2 == 0 ? w.k_alt_keys : w.k_keys, *ov = kp % 2 == 0 ? w.k_alt_vals : w.k_vals;
-  if (R > 0) {
-    LS_TRY(launch_enum_keys(false, false, R, w.dv_a, w.dk_a, w.rect, C.tiles_x, w.dstar_bits, w.refuted, w.n_refuted,
-                            w.wc_kept, nullptr, nullptr, nullptr, kp, nullptr, st));
-  }
-  // the per-warp counts are scanned like block sums: nwarps entries
-  LS_TRY(launch_dup_scan(nwarps * DUP_BLOCK, w.wc_kept, key_capacity, w.n_kept, w.n_kept_valid, status_dev, st));
+  EnumArgs ea{};
+  ea.R = R;
+  ea.order = w.dv_a;
+  ea.dkey_sorted = w.dk_a;
+  ea.rect_sorted = w.rect;
+  ea.rec = pp.rec;
+  ea.cams = T;
+  ea.n_per_cam = n;
+  ea.tile_w = P.tile_w;
+  ea.tile_h = P.tile_h;
+  ea.dstar_bits = w.dstar_bits;
+  ea.refuted = w.refuted;
+  ea.sat = w.sat;
+  ea.n_refuted = w.n_refuted;
+  ea.key_passes = kp;
+  ea.key_total = w.key_total;
+  ea.has_held = w.has_held;
+  ea.warp_counts = w.wc_kept;
+  ea.n_valid = w.n_kept_valid;
+  LS_TRY(launch_enum_keys(false, ENUM_KEPT, ea, st));
+  LS_TRY(launch_dup_scan(enum_warps(R), w.wc_kept, key_capacity, w.n_kept, w.n_kept_valid, status_dev, st));
   if (R > 0 && key_capacity > 0) {
-    LS_TRY(launch_enum_keys(true, false, R, w.dv_a, w.dk_a, w.rect, C.tiles_x, w.dstar_bits, w.refuted, w.n_refuted,
-                            w.wc_kept, w.n_kept_valid, ek, ev, kp, ks.hist, st));
+    ea.keys = ek;
+    ea.vals = ev;
+    ea.tile_hist = ks.hist;
+    LS_TRY(launch_enum_keys(true, ENUM_KEPT, ea, st));
     ls_status s = tile_sort(ek, ev, ok, ov, w.n_kept_valid, key_capacity, kp, ks, w.k_ranges, tiles, status_dev, st);
     if (s != LS_OK) return s;
   } else {
@@ -657,23 +695,27 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   }
   TruncArgs ta{};
   ta.t_thr = t_thr;
-  ta.tile_total = w.tile_total;
+  ta.has_held = w.has_held;
   ta.refuted = w.refuted;
   ta.n_refuted = w.n_refuted;
   ta.kept_ranges = reinterpret_cast<const int2*>(w.k_ranges);
   LS_TRY(launch_blend_trunc(1, pp.rec, C, P, reinterpret_cast<const int2*>(w.k_ranges), w.k_vals, image, t_final,
                             n_last, ta, st));
   // held-out keys of refuted tiles (every kernel returns at once when none)
+  LS_TRY(launch_refuted_sat(w.refuted, w.n_refuted, C.tiles_x, C.tiles_y, w.sat, st));
   uint32_t *hk = kp % 2 == 0 ? w.h_keys : w.h_alt_keys, *hv = kp % 2 == 0 ? w.h_vals : w.h_alt_vals;
   uint32_t *hok = kp % 2 == 0 ? w.h_alt_keys : w.h_keys, *hov = kp % 2 == 0 ? w.h_alt_vals : w.h_vals;
-  if (R > 0) {
-    LS_TRY(launch_enum_keys(false, true, R, w.dv_a, w.dk_a, w.rect, C.tiles_x, w.dstar_bits, w.refuted, w.n_refuted,
-                            w.wc_held, nullptr, nullptr, nullptr, kp, nullptr, st));
-  }
-  LS_TRY(launch_dup_scan(nwarps * DUP_BLOCK, w.wc_held, key_capacity, w.n_held, w.n_held_valid, status_dev, st));
+  ea.warp_counts = w.wc_held;
+  ea.n_valid = w.n_held_valid;
+  ea.keys = ea.vals = nullptr;
+  ea.tile_hist = nullptr;
+  LS_TRY(launch_enum_keys(false, ENUM_HELD, ea, st));
+  LS_TRY(launch_dup_scan(enum_warps(R), w.wc_held, key_capacity, w.n_held, w.n_held_valid, status_dev, st));
   if (R > 0 && key_capacity > 0) {
-    LS_TRY(launch_enum_keys(true, true, R, w.dv_a, w.dk_a, w.rect, C.tiles_x, w.dstar_bits, w.refuted, w.n_refuted,
-                            w.wc_held, w.n_held_valid, hk, hv, kp, hs.hist, st));
+    ea.keys = hk;
+    ea.vals = hv;
+    ea.tile_hist = hs.hist;
+    LS_TRY(launch_enum_keys(true, ENUM_HELD, ea, st));
     ls_status s = tile_sort(hk, hv, hok, hov, w.n_held_valid, key_capacity, kp, hs, w.h_ranges, tiles, status_dev, st);
     if (s != LS_OK) return s;
   } else {

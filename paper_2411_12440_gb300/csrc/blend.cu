@@ -130,6 +130,9 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
         const float l01dy = __fmul_rn(a.w, dy);
         const float e2 = __fmul_rn(bb.x, dy);
         const float e2s = __fmul_rn(e2, e2);
+        // q = fma(e1, e1, e2s) >= e2s for every pixel of the row: the whole
+        // strip is outside the support when the row term alone is
+        if (e2s > bb.z) continue;
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
           float dx, e1;
@@ -163,7 +166,7 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
 #pragma unroll
     for (int p = 0; p < PPT; ++p) settled = settled && (((done >> p) & 1u) || T[p] < ta.t_thr);
     const bool all_settled = __syncthreads_and(settled);
-    raw = !all_settled && ta.tile_total[tile_gid] > n;
+    raw = !all_settled && ta.has_held[tile_gid];
     if (raw && threadIdx.x == 0) {
       ta.refuted[tile_gid] = 1;
       atomicAdd(ta.n_refuted, 1u);
@@ -377,8 +380,10 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
 #pragma unroll
       for (int m = 0; m < 9; ++m) v[m] = 0.f;
       bool any = false;
+      const bool row_in = e2s <= bb.z;  // else q >= e2s > rho^2 for the whole strip
 #pragma unroll
       for (int p = 0; p < PPT; ++p) {
+        if (!row_in) break;
         float dx, e1;
         const float q = pair_q(xs[p], a.x, a.z, l01dy, e2s, dx, e1);
         if (j >= last[p] || q > bb.z) continue;
@@ -387,7 +392,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
         if (alpha < P.alpha_min) continue;
         any = true;
         const float4 c = s_c[jj];
-        const float iom = 1.f / (1.f - alpha);
+        const float iom = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 1 - alpha_max
         const float Tb = T[p] * iom;  // transmittance in front of this entry
         const float wgt = alpha * Tb;
         v[6] += wgt * gC0[p];
@@ -404,7 +409,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
           float gD = bb.y * ga * kern_df<KID>(xk) * P.inv_lambda;
           if (P.ags == 1) gD *= __expf(-D * D);
           else if (P.ags == 2) gD *= __expf(-xk * xk);
-          const float gq = D > 0.f ? 0.5f * gD / D : 0.f;
+          const float gq = D > 0.f ? 0.5f * __fdividef(gD, D) : 0.f;
           // A d = L^T (L d) = (l00 e1, l01 e1 + l11 e2)
           v[0] += -2.f * gq * (a.z * e1);
           v[1] += -2.f * gq * (a.w * e1 + bb.x * e2);

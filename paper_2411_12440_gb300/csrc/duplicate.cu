@@ -6,85 +6,76 @@
 // key of the classic pipeline is never built: the tile sort moves 8 bytes per
 // key per pass over ceil(tile bits / 8) passes instead of 12 bytes over six.
 //
+// A record gets a key for a tile of its support box only when its support
+// ellipse reaches one of the tile's pixel centres (emit.cuh, tile_touched):
+// the pairs the blend can composite are all kept, and the ~40 % of box tiles
+// that only the box corners reach are never sorted or blended.
+//
 //   dup_count : support box in tiles per record (binary32 tile rule), packed
-//               and stored in depth order; block sums of the tile counts.
-//   dup_scan  : exclusive scan of the block sums, total key count K and the
+//               and stored in depth order.
+//   enum_keys : per warp of 64 depth-ordered records, the box tiles the
+//               ellipse reaches, counted (first launch) and then, after
+//               dup_scan has turned the warp counts into offsets, written
+//               (second launch) with the digit histograms of the tile sort.
+//               The learned path (learned.cu) uses the same kernel with the
+//               proposal depth (kept keys) and the refuted tiles (held-out
+//               keys) as extra conditions.
+//   dup_scan  : exclusive scan of the warp counts, total key count K and the
 //               capacity check.
-//   dup_emit  : block-level prefix of the counts, then each warp writes the
-//               keys of its 128 records cooperatively (lane e of the warp's
-//               output range finds its record by binary search), so stores
-//               are coalesced whatever the footprint sizes; the digit
-//               histograms of the tile sort are gathered on the way.
+#include "emit.cuh"
 #include "kernels.h"
 
 namespace ls {
 
 namespace {
 
-struct CamLite {
-  int W, H, tiles_x, tile_base;
-};
-
-__device__ __forceinline__ uint32_t rect_count(uint2 rc) {
-  int x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF, y1 = rc.y >> 16;
-  return x1 < x0 ? 0u : (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
-}
 
 __global__ void __launch_bounds__(DUP_THREADS) dup_count_kernel(int64_t R, const uint32_t* __restrict__ order,
                                                                 const uint32_t* __restrict__ dkey_sorted,
                                                                 const float4* __restrict__ foot, const CamTable cams,
                                                                 int n_per_cam, const ParDev P,
-                                                                uint2* __restrict__ rect_sorted,
-                                                                uint32_t* __restrict__ block_sums) {
+                                                                uint2* __restrict__ rect_sorted) {
   __shared__ CamLite s_cam[LS_MAX_CAMS];
-  __shared__ uint32_t s_red[DUP_THREADS / 32];
   for (int c = threadIdx.x; c < cams.n; c += blockDim.x)
     s_cam[c] = CamLite{cams.c[c].W, cams.c[c].H, cams.c[c].tiles_x, cams.c[c].tile_base};
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * DUP_BLOCK;
-  uint32_t sum = 0;
-#pragma unroll
-  for (int i = 0; i < DUP_ITEMS; ++i) {
-    const int64_t j = base + i * DUP_THREADS + threadIdx.x;
-    if (j >= R) break;
-    uint2 rc = make_uint2(1u, 0u);  // empty: x1 < x0
-    if (dkey_sorted[j] != DKEY_CULLED) {
-      const uint32_t r = order[j];
-      const CamLite cm = s_cam[r / (uint32_t)n_per_cam];
-      const float4 f = foot[r];
-      int tx0, tx1, ty0, ty1;
-      if (tile_rect(f.x, f.y, f.z, f.w, cm.W, cm.H, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1))
-        rc = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
-    }
-    rect_sorted[j] = rc;
-    sum += rect_count(rc);
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= R) return;
+  uint2 rc = make_uint2(1u, 0u);  // empty: x1 < x0
+  if (dkey_sorted[j] != DKEY_CULLED) {
+    const uint32_t r = order[j];
+    const CamLite cm = s_cam[cams.n > 1 ? r / (uint32_t)n_per_cam : 0u];
+    const float4 f = foot[r];
+    int tx0, tx1, ty0, ty1;
+    if (tile_rect(f.x, f.y, f.z, f.w, cm.W, cm.H, P.tile_w, P.tile_h, tx0, tx1, ty0, ty1))
+      rc = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = sum;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t t = 0;
-    for (int w = 0; w < DUP_THREADS / 32; ++w) t += s_red[w];
-    block_sums[blockIdx.x] = t;
-  }
+  rect_sorted[j] = rc;
 }
 
-// One block scans all block sums in chunks of 1024 (exclusive, in place).
-__global__ void __launch_bounds__(1024) dup_scan_kernel(int64_t nb, uint32_t* sums, int64_t cap, int64_t* n_keys,
+// One block scans the warp counts (exclusive, in place), 16 consecutive
+// entries per thread and 16384 per round.
+__global__ void __launch_bounds__(1024) dup_scan_kernel(int64_t n, uint32_t* counts, int64_t cap, int64_t* n_keys,
                                                         int64_t* n_valid, int32_t* status) {
+  constexpr int PER = 16;
   __shared__ uint64_t s_warp[32];
   __shared__ uint64_t s_carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
-  for (int64_t b0 = 0; b0 < nb; b0 += 1024) {
-    const int64_t i = b0 + threadIdx.x;
-    uint64_t v = i < nb ? sums[i] : 0;
-    uint64_t x = v;
+  for (int64_t b0 = 0; b0 < n; b0 += (int64_t)PER * 1024) {
+    const int64_t i0 = b0 + (int64_t)PER * threadIdx.x;
+    uint32_t v[PER];
+    uint64_t run = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      v[k] = i0 + k < n ? counts[i0 + k] : 0u;
+      run += v[k];
+    }
+    uint64_t x = run;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint64_t u = __shfl_up_sync(0xffffffffu, x, o);
+      const uint64_t u = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += u;
     }
     if (lane == 31) s_warp[warp] = x;
@@ -93,16 +84,20 @@ __global__ void __launch_bounds__(1024) dup_scan_kernel(int64_t nb, uint32_t* su
       uint64_t w = s_warp[lane];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        uint64_t u = __shfl_up_sync(0xffffffffu, w, o);
+        const uint64_t u = __shfl_up_sync(0xffffffffu, w, o);
         if (lane >= o) w += u;
       }
       s_warp[lane] = w;
     }
     __syncthreads();
-    const uint64_t incl = x + (warp > 0 ? s_warp[warp - 1] : 0) + s_carry;
-    if (i < nb) sums[i] = (uint32_t)(incl - v);
+    uint64_t ex = x - run + (warp > 0 ? s_warp[warp - 1] : 0) + s_carry;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      if (i0 + k < n) counts[i0 + k] = (uint32_t)ex;
+      ex += v[k];
+    }
     __syncthreads();
-    if (threadIdx.x == 1023) s_carry = incl;
+    if (threadIdx.x == 1023) s_carry = ex;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -114,119 +109,170 @@ __global__ void __launch_bounds__(1024) dup_scan_kernel(int64_t nb, uint32_t* su
   }
 }
 
-__global__ void __launch_bounds__(DUP_THREADS) dup_emit_kernel(int64_t R, const uint32_t* __restrict__ order,
-                                                               const uint2* __restrict__ rect_sorted,
-                                                               const uint32_t* __restrict__ block_offs,
-                                                               const CamTable cams, int n_per_cam,
-                                                               const int64_t* n_valid, uint32_t* __restrict__ keys,
-                                                               uint32_t* __restrict__ vals, int key_passes,
-                                                               uint32_t* __restrict__ tile_hist) {
-  __shared__ uint32_t s_off[DUP_BLOCK + 1];
-  __shared__ uint2 s_rect[DUP_BLOCK];
-  __shared__ uint32_t s_r[DUP_BLOCK];
-  __shared__ uint32_t s_hist[3][RADIX];
-  __shared__ uint32_t s_warp[DUP_THREADS / 32];
+// The condition of each mode on a reached candidate (key, record depth bits):
+// ENUM_ALL none; ENUM_KEPT depth bits <= the tile's proposal; ENUM_HELD the
+// tile is refuted and the depth is beyond its proposal.  In the count launch
+// of ENUM_KEPT a reached key beyond the proposal flags its tile in has_held.
+template <int MODE, bool COUNT>
+__device__ __forceinline__ bool cand_taken(const EnumArgs& A, const EnumRec& t, int tx, int ty, uint32_t key,
+                                           uint32_t& reached) {
+  if (!tile_reached(t, tx, ty, A.tile_w, A.tile_h)) return false;
+  if (MODE == ENUM_ALL) return true;
+  ++reached;
+  const uint32_t lim = __ldg(A.dstar_bits + key);
+  if (MODE == ENUM_KEPT) {
+    const bool kept = t.dk <= lim;
+    if (COUNT && !kept && !__ldg(A.has_held + key)) A.has_held[key] = 1;
+    return kept;
+  }
+  return A.refuted[key] && t.dk > lim;
+}
+
+// Keys of ENUM_WARP_RECS depth-ordered records per warp (emit.cuh).  EMIT =
+// false writes each warp's count (and, in ENUM_KEPT, adds every reached key
+// to *key_total and flags tiles in has_held); EMIT = true writes the keys at
+// the warp's scanned offset and the tile-sort digit histograms.  ENUM_HELD
+// drops up front every record whose box holds no refuted tile (summed-area
+// table `sat`).
+template <bool EMIT, int MODE>
+__global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
+  __shared__ EnumRec S[ENUM_WARPS][ENUM_WARP_RECS];
   __shared__ CamLite s_cam[LS_MAX_CAMS];
-  if (*n_valid == 0) return;  // nothing to emit, or over capacity
+  __shared__ uint32_t s_hist[EMIT ? 3 : 1][RADIX];
+  const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int c = tid; c < cams.n; c += DUP_THREADS)
-    s_cam[c] = CamLite{cams.c[c].W, cams.c[c].H, cams.c[c].tiles_x, cams.c[c].tile_base};
-  for (int i = tid; i < 3 * RADIX; i += DUP_THREADS) (&s_hist[0][0])[i] = 0;
-  const int64_t base = (int64_t)blockIdx.x * DUP_BLOCK;
-  // coalesced load of the block's records
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t gw = (int64_t)blockIdx.x * ENUM_WARPS + warp;
+  if ((MODE == ENUM_HELD && *A.n_refuted == 0u) || (EMIT && *A.n_valid == 0)) {
+    if (!EMIT && lane == 0) A.warp_counts[gw] = 0u;
+    return;  // block-uniform: nothing to do, or over capacity
+  }
+  for (int c = tid; c < A.cams.n; c += ENUM_THREADS)
+    s_cam[c] = CamLite{A.cams.c[c].W, A.cams.c[c].H, A.cams.c[c].tiles_x, A.cams.c[c].tile_base};
+  if (EMIT)
+    for (int i = tid; i < 3 * RADIX; i += ENUM_THREADS) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  // the warp's records with candidates, compacted, with their offsets
+  EnumRec* W = S[warp];
+  int n_nz = 0;
+  uint32_t total = 0;
+  const int sx = s_cam[0].tiles_x + 1;
 #pragma unroll
-  for (int i = 0; i < DUP_ITEMS; ++i) {
-    const int s = i * DUP_THREADS + tid;
-    const int64_t j = base + s;
+  for (int i = 0; i < ENUM_WARP_RECS / 32; ++i) {
+    const int64_t j = (int64_t)blockIdx.x * ENUM_BLOCK_RECS + warp * ENUM_WARP_RECS + i * 32 + lane;
     uint2 rc = make_uint2(1u, 0u);
-    uint32_t r = 0;
-    if (j < R) {
-      rc = rect_sorted[j];
-      r = order[j];
+    uint32_t r = 0, dk = DKEY_CULLED;
+    if (j < A.R) {
+      rc = A.rect_sorted[j];
+      r = A.order[j];
+      if (MODE != ENUM_ALL) dk = A.dkey_sorted[j];
     }
-    s_rect[s] = rc;
-    s_r[s] = r;
-  }
-  __syncthreads();
-  // block exclusive scan of the counts: thread t owns slots 4t..4t+3
-  uint32_t c[DUP_ITEMS], run = 0;
-#pragma unroll
-  for (int i = 0; i < DUP_ITEMS; ++i) {
-    c[i] = rect_count(s_rect[DUP_ITEMS * tid + i]);
-    run += c[i];
-  }
-  uint32_t x = run;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += u;
-  }
-  if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
-  uint32_t wpre = 0;
-  for (int w = 0; w < warp; ++w) wpre += s_warp[w];
-  uint32_t ex = x - run + wpre;
-#pragma unroll
-  for (int i = 0; i < DUP_ITEMS; ++i) {
-    s_off[DUP_ITEMS * tid + i] = ex;
-    ex += c[i];
-  }
-  if (tid == DUP_THREADS - 1) s_off[DUP_BLOCK] = ex;
-  __syncthreads();
-  // warp w emits slots [w*128, w*128+128)
-  const int s0 = warp * 32 * DUP_ITEMS, s1 = s0 + 32 * DUP_ITEMS;
-  const uint32_t o0 = s_off[s0], o1 = s_off[s1];
-  const uint64_t gbase = (uint64_t)block_offs[blockIdx.x];
-  for (uint32_t e = o0 + lane; e < o1; e += 32) {
-    // last slot in [s0, s1) whose offset is <= e
-    int lo = s0, hi = s1 - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= e) lo = mid;
-      else hi = mid - 1;
+    uint32_t cnt = box_count(rc);
+    if (MODE == ENUM_HELD && cnt) {
+      const int x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF, y1 = rc.y >> 16;
+      const int* sat = A.sat;
+      if (sat[(y1 + 1) * sx + x1 + 1] - sat[y0 * sx + x1 + 1] - sat[(y1 + 1) * sx + x0] + sat[y0 * sx + x0] == 0)
+        cnt = 0u;
     }
-    const uint2 rc = s_rect[lo];
-    const uint32_t r = s_r[lo];
-    const uint32_t m = e - s_off[lo];
-    const uint32_t x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF;
-    const uint32_t w = x1 - x0 + 1;
-    const CamLite cm = s_cam[r / (uint32_t)n_per_cam];
-    const uint32_t key = (uint32_t)cm.tile_base + (y0 + m / w) * (uint32_t)cm.tiles_x + x0 + m % w;
-    keys[gbase + e] = key;
-    vals[gbase + e] = r;
-    for (int p = 0; p < key_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
+    uint32_t x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += u;
+    }
+    const unsigned nz = __ballot_sync(FULL, cnt > 0);
+    if (cnt) {
+      EnumRec& t = W[n_nz + __popc(nz & lt)];
+      const CamLite cm = s_cam[A.cams.n > 1 ? r / (uint32_t)A.n_per_cam : 0u];
+      enum_rec(t, rc, r, dk, cm, A.rec);
+      t.off = total + x - cnt;
+    }
+    n_nz += __popc(nz);
+    total += __shfl_sync(FULL, x, 31);
+  }
+  __syncwarp();
+  const uint64_t out = EMIT ? A.out_base + (uint64_t)A.warp_counts[gw] : 0u;
+  uint32_t kept = 0, reached = 0;
+  int sp = 0;  // record of the step's first candidate
+  for (uint32_t cb = 0; cb < total; cb += 32) {
+    // lane i marks where record sp + 1 + i starts, when inside this step;
+    // lane l's record is sp plus the number of marks at or below l
+    const int ns = sp + 1 + lane;
+    uint32_t mark = 0;
+    if (ns < n_nz) {
+      const uint32_t d = W[ns].off - cb;
+      if (d < 32u) mark = 1u << d;
+    }
+    const uint32_t M = __reduce_or_sync(FULL, mark);
+    const int sl = sp + __popc(M & ((2u << lane) - 1u));
+    const uint32_t e = cb + lane;
+    bool take = false;
+    uint32_t key = 0;
+    if (e < total) {
+      int tx, ty;
+      key = cand_key(W[sl], e - W[sl].off, tx, ty);
+      take = cand_taken<MODE, !EMIT>(A, W[sl], tx, ty, key, reached);
+    }
+    sp = __shfl_sync(FULL, sl, 31);
+    const unsigned bal = __ballot_sync(FULL, take);
+    if (EMIT && take) {
+      const uint64_t pos = out + kept + __popc(bal & lt);
+      A.keys[pos] = key;
+      A.vals[pos] = W[sl].r;
+      for (int p = 0; p < A.key_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
+    }
+    kept += __popc(bal);
+  }
+  if (!EMIT) {
+    if (MODE == ENUM_KEPT) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) reached += __shfl_xor_sync(FULL, reached, o);
+    }
+    if (lane == 0) {
+      A.warp_counts[gw] = kept;
+      if (MODE == ENUM_KEPT && reached) atomicAdd(A.key_total, (unsigned long long)reached);
+    }
+    return;
   }
   __syncthreads();
-  for (int i = tid; i < key_passes * RADIX; i += DUP_THREADS) {
+  for (int i = tid; i < A.key_passes * RADIX; i += ENUM_THREADS) {
     const uint32_t v = (&s_hist[0][0])[i];
-    if (v) atomicAdd(&tile_hist[i], v);
+    if (v) atomicAdd(&A.tile_hist[i], v);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_dup_count(int64_t R, const uint32_t* order, const uint32_t* dkey_sorted, const float4* foot,
-                             const CamTable& cams, int n_per_cam, const ParDev& P, uint2* rect_sorted,
-                             uint32_t* block_sums, cudaStream_t st) {
+                             const CamTable& cams, int n_per_cam, const ParDev& P, uint2* rect_sorted, cudaStream_t st) {
   if (R == 0) return cudaSuccess;
-  dup_count_kernel<<<ceil_div(R, DUP_BLOCK), DUP_THREADS, 0, st>>>(R, order, dkey_sorted, foot, cams, n_per_cam, P,
-                                                                  rect_sorted, block_sums);
+  dup_count_kernel<<<ceil_div(R, DUP_THREADS), DUP_THREADS, 0, st>>>(R, order, dkey_sorted, foot, cams, n_per_cam, P,
+                                                                    rect_sorted);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dup_scan(int64_t R, uint32_t* block_sums, int64_t cap, int64_t* n_keys_dev, int64_t* n_valid_dev,
+cudaError_t launch_dup_scan(int64_t n, uint32_t* counts, int64_t cap, int64_t* n_keys_dev, int64_t* n_valid_dev,
                             int32_t* status, cudaStream_t st) {
-  dup_scan_kernel<<<1, 1024, 0, st>>>(R > 0 ? (int64_t)ceil_div(R, DUP_BLOCK) : 0, block_sums, cap, n_keys_dev,
-                                      n_valid_dev, status);
+  dup_scan_kernel<<<1, 1024, 0, st>>>(n, counts, cap, n_keys_dev, n_valid_dev, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dup_emit(int64_t R, const uint32_t* order, const uint2* rect_sorted, const uint32_t* block_offs,
-                            const CamTable& cams, int n_per_cam, const int64_t* n_valid_dev, uint32_t* keys,
-                            uint32_t* vals, int key_passes, uint32_t* tile_hist, cudaStream_t st) {
-  if (R == 0) return cudaSuccess;
-  dup_emit_kernel<<<ceil_div(R, DUP_BLOCK), DUP_THREADS, 0, st>>>(R, order, rect_sorted, block_offs, cams, n_per_cam,
-                                                                 n_valid_dev, keys, vals, key_passes, tile_hist);
+int64_t enum_warps(int64_t R) { return R > 0 ? (int64_t)ceil_div(R, ENUM_BLOCK_RECS) * ENUM_WARPS : 0; }
+
+cudaError_t launch_enum_keys(bool emit, int mode, const EnumArgs& A, cudaStream_t st) {
+  if (A.R == 0) return cudaSuccess;
+  const unsigned grid = ceil_div(A.R, ENUM_BLOCK_RECS);
+#define LS_EK(E, M) enum_keys_kernel<E, M><<<grid, ENUM_THREADS, 0, st>>>(A)
+  if (emit) {
+    if (mode == ENUM_ALL) LS_EK(true, ENUM_ALL);
+    else if (mode == ENUM_KEPT) LS_EK(true, ENUM_KEPT);
+    else LS_EK(true, ENUM_HELD);
+  } else {
+    if (mode == ENUM_ALL) LS_EK(false, ENUM_ALL);
+    else if (mode == ENUM_KEPT) LS_EK(false, ENUM_KEPT);
+    else LS_EK(false, ENUM_HELD);
+  }
+#undef LS_EK
   return cudaGetLastError();
 }
 

@@ -52,16 +52,42 @@ cudaError_t launch_ranges_fixup(int32_t* ranges, int total_tiles, cudaStream_t s
 
 // ---- duplication and tile ranges (duplicate.cu)
 constexpr int DUP_THREADS = 256;
-constexpr int DUP_ITEMS = 4;
+constexpr int DUP_ITEMS = 2;
 constexpr int DUP_BLOCK = DUP_THREADS * DUP_ITEMS;
 cudaError_t launch_dup_count(int64_t R, const uint32_t* order, const uint32_t* dkey_sorted, const float4* foot,
-                             const CamTable& cams, int n_per_cam, const ParDev& P, uint2* rect_sorted,
-                             uint32_t* block_sums, cudaStream_t st);
-cudaError_t launch_dup_scan(int64_t R, uint32_t* block_sums, int64_t cap, int64_t* n_keys_dev, int64_t* n_valid_dev,
+                             const CamTable& cams, int n_per_cam, const ParDev& P, uint2* rect_sorted, cudaStream_t st);
+// Exclusive scan of n counts in place; *n_keys_dev = total, *n_valid_dev =
+// total when it fits cap (else 0, and LS_ERR_CAPACITY in *status).
+cudaError_t launch_dup_scan(int64_t n, uint32_t* counts, int64_t cap, int64_t* n_keys_dev, int64_t* n_valid_dev,
                             int32_t* status, cudaStream_t st);
-cudaError_t launch_dup_emit(int64_t R, const uint32_t* order, const uint2* rect_sorted, const uint32_t* block_offs,
-                            const CamTable& cams, int n_per_cam, const int64_t* n_valid_dev, uint32_t* keys,
-                            uint32_t* vals, int key_passes, uint32_t* tile_hist, cudaStream_t st);
+
+// Key enumeration (duplicate.cu): which keys of the depth-ordered records'
+// support boxes are taken.
+enum { ENUM_ALL = 0, ENUM_KEPT = 1, ENUM_HELD = 2 };
+struct EnumArgs {
+  int64_t R;                      // records in depth order
+  const uint32_t* order;          // [R] record id at each depth rank
+  const uint32_t* dkey_sorted;    // [R] depth bits (ENUM_KEPT, ENUM_HELD)
+  const uint2* rect_sorted;       // [R] packed tile box, empty when x1 < x0
+  const float4* rec;              // [R][3] projected records (ellipse of each)
+  CamTable cams;                  // tile_base / tiles_x of each camera
+  int n_per_cam;
+  int tile_w, tile_h;
+  const uint32_t* dstar_bits;     // [tiles] proposal depth bits (ENUM_KEPT, ENUM_HELD)
+  const uint8_t* refuted;         // [tiles] (ENUM_HELD)
+  const int* sat;                 // summed-area table of refuted (ENUM_HELD)
+  const unsigned* n_refuted;      // (ENUM_HELD)
+  uint32_t* warp_counts;          // [enum_warps(R)] taken keys per warp, then scanned offsets
+  const int64_t* n_valid;         // total that fits the capacity (emit)
+  uint64_t out_base;              // emit: first output position
+  uint32_t *keys, *vals;          // emit outputs
+  int key_passes;
+  uint32_t* tile_hist;            // [key_passes][RADIX] digit counts (emit)
+  unsigned long long* key_total;  // ENUM_KEPT count launch: all keys reached
+  uint8_t* has_held;              // ENUM_KEPT count launch: [tiles] set for tiles with keys beyond the proposal
+};
+int64_t enum_warps(int64_t R);
+cudaError_t launch_enum_keys(bool emit, int mode, const EnumArgs& A, cudaStream_t st);
 
 // ---- blending (blend.cu)
 // Pixel offset of each camera's image in a batched render's packed output.
@@ -76,7 +102,7 @@ cudaError_t launch_blend_batch(const float4* rec, const uint32_t* vals, const in
 // Extra inputs/outputs of the truncated, resumed and labelled forwards.
 struct TruncArgs {
   float t_thr;                // a pixel with T < t_thr counts as settled
-  const int32_t* tile_total;  // keys touching each tile before truncation
+  const uint8_t* has_held;    // [tiles] set when the tile has keys beyond its proposal
   uint8_t* refuted;           // [tiles] set for refuted tiles
   unsigned* n_refuted;
   const int2* kept_ranges;    // resume: the kept list of each tile
@@ -109,10 +135,9 @@ cudaError_t launch_features(void* planes, const CamDev& cam, const ParDev& P, vo
                             unsigned long long* key_total, cudaStream_t st);
 cudaError_t launch_dstar(int ntiles, const float* y, float margin, const float* dstar_in, uint32_t* bits,
                          float* dstar_out, cudaStream_t st);
-cudaError_t launch_enum_keys(bool emit, bool held, int64_t R, const uint32_t* order, const uint32_t* dkey_sorted,
-                             const uint2* rect_sorted, int tiles_x, const uint32_t* dstar_bits, const uint8_t* refuted,
-                             const unsigned* n_refuted, uint32_t* warp_counts, const int64_t* n_valid, uint32_t* keys,
-                             uint32_t* vals, int key_passes, uint32_t* tile_hist, cudaStream_t st);
+// Summed-area table of the refuted flags, (tiles_x + 1) x (tiles_y + 1) ints.
+cudaError_t launch_refuted_sat(const uint8_t* refuted, const unsigned* n_refuted, int tiles_x, int tiles_y, int* sat,
+                               cudaStream_t st);
 cudaError_t launch_learned_stats(const unsigned long long* key_total, const int64_t* n_kept, const int64_t* n_held,
                                  const unsigned* n_refuted, int64_t* stats, cudaStream_t st);
 

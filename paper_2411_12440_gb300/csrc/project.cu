@@ -250,8 +250,11 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(int n, const float* __
 }
 
 // a6: hand-derived chain rule, recomputing the forward intermediates.
-template <int DEG>
-__global__ void __launch_bounds__(128) project_bwd_kernel(int n, const float* __restrict__ means,
+// ONE: a single camera, so the SH gradient of each channel is final as soon
+// as it is formed and is stored at once instead of being held (3 (D+1)^2
+// accumulators) across cameras; the kernel then fits twice the warps per SM.
+template <int DEG, bool ONE>
+__global__ void __launch_bounds__(ONE ? 256 : 128, ONE ? 2 : 1) project_bwd_kernel(int n, const float* __restrict__ means,
                                                           const float* __restrict__ scales,
                                                           const float4* __restrict__ quats,
                                                           const float* __restrict__ opac,
@@ -268,9 +271,11 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(int n, const float* __
   float4 qv = quats[i];
   float o = opac[i];
   float gmu[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
-  float gsh[K][3];
+  constexpr int KA = ONE ? 1 : K;  // SH accumulators held across cameras
+  float gsh[KA][3];
 #pragma unroll
-  for (int k = 0; k < K; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
+  for (int k = 0; k < KA; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
+  bool sh_written = false;
 
   for (int c = 0; c < cams.n; ++c) {
     size_t r = (size_t)c * n + i;
@@ -299,10 +304,12 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(int n, const float* __
       float gc = v > 0.f ? grgb[ch] : 0.f;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        gsh[k][ch] += gc * Y[k];
+        if (ONE) g_sh[(size_t)(3 * k + ch) * n + i] = gc * Y[k];
+        else gsh[k][ch] += gc * Y[k];
         wsum[k] += gc * sh[(size_t)(3 * k + ch) * n + i];
       }
     }
+    sh_written = ONE;
     if (DEG > 0) {
       float gdx, gdy, gdz;
       sh_basis_grad<DEG>(s.dir[0], s.dir[1], s.dir[2], wsum, gdx, gdy, gdz);
@@ -402,10 +409,12 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(int n, const float* __
   g_scales[3 * i + 2] = gs[2];
   g_quats[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
   g_opac[i] = go;
+  if (!sh_written) {
 #pragma unroll
-  for (int k = 0; k < K; ++k)
+    for (int k = 0; k < K; ++k)
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) g_sh[(size_t)(3 * k + ch) * n + i] = gsh[k][ch];
+      for (int ch = 0; ch < 3; ++ch) g_sh[(size_t)(3 * k + ch) * n + i] = ONE ? 0.f : gsh[k][ch];
+  }
 }
 
 cudaError_t launch_project_fwd(int n, const float* means, const float* scales, const float* quats,
@@ -428,17 +437,26 @@ cudaError_t launch_project_bwd(int n, const float* means, const float* scales, c
                                ProjCPtr proj, const float* g2d, float* g_means, float* g_scales, float* g_quats,
                                float* g_opac, float* g_sh, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  dim3 grid(ceil_div(n, 128));
   const float4* q4 = reinterpret_cast<const float4*>(quats);
   const float4* g4 = reinterpret_cast<const float4*>(g2d);
   float4* gq4 = reinterpret_cast<float4*>(g_quats);
-#define LS_PB(D) project_bwd_kernel<D><<<grid, 128, 0, st>>>(n, means, scales, q4, opac, sh, cams, P, proj, g4, \
+#define LS_PB(D, ONE, TB)                                                                                  \
+  project_bwd_kernel<D, ONE><<<ceil_div(n, TB), TB, 0, st>>>(n, means, scales, q4, opac, sh, cams, P, proj, g4, \
                                                              g_means, g_scales, gq4, g_opac, g_sh)
-  switch (P.sh_degree) {
-    case 0: LS_PB(0); break;
-    case 1: LS_PB(1); break;
-    case 2: LS_PB(2); break;
-    default: LS_PB(3); break;
+  if (cams.n == 1) {
+    switch (P.sh_degree) {
+      case 0: LS_PB(0, true, 256); break;
+      case 1: LS_PB(1, true, 256); break;
+      case 2: LS_PB(2, true, 256); break;
+      default: LS_PB(3, true, 256); break;
+    }
+  } else {
+    switch (P.sh_degree) {
+      case 0: LS_PB(0, false, 128); break;
+      case 1: LS_PB(1, false, 128); break;
+      case 2: LS_PB(2, false, 128); break;
+      default: LS_PB(3, false, 128); break;
+    }
   }
 #undef LS_PB
   return cudaGetLastError();

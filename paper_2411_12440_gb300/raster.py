@@ -184,7 +184,8 @@ class Rasterizer:
         return proj, tc
 
     def ensure_capacity(self, tile_counts):
-        """Size the key buffers from the exact count (one device->host read)."""
+        """Size the key buffers from the support-box tile count, an upper bound
+        on the keys (one device->host read)."""
         K = int(tile_counts.sum(dtype=torch.int64).item())
         if K > self.capacity:
             self.capacity = int(math.ceil(K * self.grow_margin)) + 1024

@@ -79,7 +79,12 @@ def test_batch_capacity_overflow_is_reported():
     scene, cams = _scene_and_cams(n=5000, n_cams=2, seed=5)
     sp = raster.Splats.from_scene(scene)
     br = BatchRenderer(sp, cams, raster.RenderParams(sh_degree=3))
-    K = br.count_keys()
+    br.plan()
+    br.render_eager()
+    torch.cuda.synchronize()
+    br.check()
+    K = int(br.n_keys.item())
+    assert 0 < K <= br.count_keys()
     br.plan(capacity=K - 1)
     br.render_eager()
     torch.cuda.synchronize()

@@ -451,3 +451,42 @@ def test_tile_depth_hist_brute_force():
     assert np.array_equal(counts, exp) and counts.sum() > 0
     assert (np.diff(cov, axis=1) >= 0).all()
     assert cov[:, -1].sum() == pytest.approx(total_w, rel=1e-9)
+
+
+@pytest.mark.parametrize("tw,th", [(16, 16), (8, 8), (32, 16)])
+def test_touch_pairs_are_the_tiles_holding_support_pixels(tw, th):
+    """The pairs every tile list must hold: brute force over every pixel of
+    the image — a tile is reached iff one of its pixel centres lies in the
+    (shrunk) support ellipse — and they are a subset of the box lists."""
+    W, H = 70, 45
+    rec = scenes.random_records(150, W, H, seed=9, max_ext=25.0)
+    dkey = np.where(rec["visible"], rec["depth"].view(np.uint32), np.uint32(0xFFFFFFFF)).astype(np.uint32)
+    foot = np.concatenate([rec["mean2d"], rec["ext"]], 1)
+    l00, l01, l11 = (rec["chol"][:, k].astype(np.float64) for k in range(3))
+    conic = np.stack([l00 * l00, l00 * l01, l01 * l01 + l11 * l11], 1)
+    rho2 = rec["rho2"].astype(np.float64)
+    shrink = 0.9
+    t, r = oracle.touch_pairs(foot, dkey, conic, rho2, W, H, tw, th, shrink)
+    ok, ov, _ = oracle.dupsort_f32(foot, dkey, W, H, tw, th)
+    R1 = 151
+    assert np.isin(t.astype(np.int64) * R1 + r, ok.astype(np.int64) * R1 + ov).all()
+    px, py = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    tiles_x = (W + tw - 1) // tw
+    exp = set()
+    for i in range(150):
+        if dkey[i] == 0xFFFFFFFF or oracle.rect(foot[i, 0], foot[i, 1], foot[i, 2], foot[i, 3], W, H, True) is None:
+            continue
+        x0, x1, y0, y1 = oracle.rect(foot[i, 0], foot[i, 1], foot[i, 2], foot[i, 3], W, H, True)
+        dx, dy = px - np.float64(foot[i, 0]), py - np.float64(foot[i, 1])
+        q = conic[i, 0] * dx * dx + 2 * conic[i, 1] * dx * dy + conic[i, 2] * dy * dy
+        inside = (q <= shrink * rho2[i])
+        inside[:, :x0] = False
+        inside[:, x1 + 1:] = False
+        inside[:y0, :] = False
+        inside[y1 + 1:, :] = False
+        ys, xs = np.nonzero(inside)
+        for tt in set(((ys // th) * tiles_x + xs // tw).tolist()):
+            exp.add((tt, i))
+    got = set(zip(t.tolist(), r.tolist()))
+    assert got == exp
+    assert 0 < len(got) < len(ok)
