@@ -113,7 +113,9 @@ struct DupWs {
   uint32_t *dk_a, *dv_a, *dk_b, *dv_b;  // depth sort ping-pong [R]
   uint2* rect;                          // [R]
   uint32_t* warp_counts;                // [enum warps]
+  uint32_t* warp_tbase;                 // [enum warps]
   int64_t* n_valid;
+  unsigned long long* tmp_ctr;          // stash allocator (zeroed)
   uint32_t *k_alt, *v_alt;              // tile sort ping-pong [cap]
   void* depth_scratch;
   void* tile_scratch;
@@ -136,10 +138,12 @@ DupWs dup_layout(char* base, int64_t R, int64_t cap, int key_passes) {
   w.dv_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
   w.rect = reinterpret_cast<uint2*>(take(8 * Rz));
   w.warp_counts = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
+  w.warp_tbase = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
   w.n_valid = reinterpret_cast<int64_t*>(take(8));
   w.k_alt = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.v_alt = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.zero_begin = off;
+  w.tmp_ctr = reinterpret_cast<unsigned long long*>(take(8));
   w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4));
   w.tile_scratch = take(sort_scratch_bytes((int64_t)Cz, key_passes));
   w.zero_bytes = off - w.zero_begin;
@@ -230,8 +234,14 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
     LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 3, ds, nullptr, status_dev, st));
     LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n_per_cam, P, w.rect, st));
   }
-  // keys of the tiles each support ellipse reaches: count per warp, scan
-  // (total K and the capacity check), then write in depth order
+  // keys of the tiles each support ellipse reaches: count per warp (and
+  // stash them), scan (total K and the capacity check), then write in depth
+  // order.  Emission goes to the buffer that makes the last tile-sort pass
+  // end in the caller's keys/vals; the stash is the other one.
+  uint32_t* ek = (kp % 2 == 0) ? keys : w.k_alt;
+  uint32_t* ev = (kp % 2 == 0) ? vals : w.v_alt;
+  uint32_t* ok = (kp % 2 == 0) ? w.k_alt : keys;
+  uint32_t* ov = (kp % 2 == 0) ? w.v_alt : vals;
   EnumArgs ea{};
   ea.R = R;
   ea.order = w.dv_a;
@@ -243,16 +253,16 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
   ea.tile_w = P.tile_w;
   ea.tile_h = P.tile_h;
   ea.warp_counts = w.warp_counts;
+  ea.warp_tbase = w.warp_tbase;
+  ea.n_warps = enum_warps(R);
+  ea.tmp_keys = ok;
+  ea.tmp_vals = ov;
+  ea.tmp_cap = (ok && ov) ? key_capacity : 0;
+  ea.tmp_ctr = w.tmp_ctr;
   ea.n_valid = w.n_valid;
   ea.key_passes = kp;
   LS_TRY(launch_enum_keys(false, ENUM_ALL, ea, st));
   LS_TRY(launch_dup_scan(enum_warps(R), w.warp_counts, key_capacity, n_keys_dev, w.n_valid, status_dev, st));
-  // emission goes to the buffer that makes the last tile-sort pass end in
-  // the caller's keys/vals
-  uint32_t* ek = (kp % 2 == 0) ? keys : w.k_alt;
-  uint32_t* ev = (kp % 2 == 0) ? vals : w.v_alt;
-  uint32_t* ok = (kp % 2 == 0) ? w.k_alt : keys;
-  uint32_t* ov = (kp % 2 == 0) ? w.v_alt : vals;
   SortScratch ts = sort_scratch_carve(w.tile_scratch, key_capacity > 0 ? key_capacity : 1, kp);
   // ranges: accumulated by the last tile pass as (min start, ~max end)
   LS_TRY(cudaMemsetAsync(tile_ranges, 0xFF, sizeof(int32_t) * 2 * (size_t)total_tiles, st));
@@ -498,6 +508,8 @@ struct LearnedWs {
   uint32_t* dstar_bits;
   uint8_t* refuted;
   uint8_t* has_held;
+  uint32_t* warp_tbase;
+  unsigned long long *tmp_ctr_kept, *tmp_ctr_held;
   uint32_t *wc_kept, *wc_held;
   uint32_t *k_keys, *k_vals, *k_alt_keys, *k_alt_vals;
   uint32_t *h_keys, *h_vals, *h_alt_keys, *h_alt_vals;
@@ -533,6 +545,7 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
   w.dstar_bits = reinterpret_cast<uint32_t*>(take(4 * tiles));
   w.wc_kept = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
   w.wc_held = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
+  w.warp_tbase = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
   w.k_keys = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.k_vals = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.k_alt_keys = reinterpret_cast<uint32_t*>(take(4 * Cz));
@@ -549,6 +562,8 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
   w.diff = reinterpret_cast<int*>(take(4 * 33 * (size_t)(tiles_x + 1) * (tiles_y + 1)));
   w.refuted = reinterpret_cast<uint8_t*>(take(tiles));
   w.has_held = reinterpret_cast<uint8_t*>(take(tiles));
+  w.tmp_ctr_kept = reinterpret_cast<unsigned long long*>(take(8));
+  w.tmp_ctr_held = reinterpret_cast<unsigned long long*>(take(8));
   w.n_kept = reinterpret_cast<int64_t*>(take(8));
   w.n_kept_valid = reinterpret_cast<int64_t*>(take(8));
   w.n_held = reinterpret_cast<int64_t*>(take(8));
@@ -680,6 +695,12 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   ea.key_total = w.key_total;
   ea.has_held = w.has_held;
   ea.warp_counts = w.wc_kept;
+  ea.warp_tbase = w.warp_tbase;
+  ea.n_warps = enum_warps(R);
+  ea.tmp_keys = ok;
+  ea.tmp_vals = ov;
+  ea.tmp_cap = key_capacity;
+  ea.tmp_ctr = w.tmp_ctr_kept;
   ea.n_valid = w.n_kept_valid;
   LS_TRY(launch_enum_keys(false, ENUM_KEPT, ea, st));
   LS_TRY(launch_dup_scan(enum_warps(R), w.wc_kept, key_capacity, w.n_kept, w.n_kept_valid, status_dev, st));
@@ -706,6 +727,9 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   uint32_t *hk = kp % 2 == 0 ? w.h_keys : w.h_alt_keys, *hv = kp % 2 == 0 ? w.h_vals : w.h_alt_vals;
   uint32_t *hok = kp % 2 == 0 ? w.h_alt_keys : w.h_keys, *hov = kp % 2 == 0 ? w.h_alt_vals : w.h_vals;
   ea.warp_counts = w.wc_held;
+  ea.tmp_keys = hok;
+  ea.tmp_vals = hov;
+  ea.tmp_ctr = w.tmp_ctr_held;
   ea.n_valid = w.n_held_valid;
   ea.keys = ea.vals = nullptr;
   ea.tile_hist = nullptr;

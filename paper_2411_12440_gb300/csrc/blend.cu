@@ -324,14 +324,14 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
   const int py = J.y0 + lr, px0 = J.x0 + lc;
   const float y = (float)py + 0.5f;
   const int lane = threadIdx.x & 31;
-  float xs[PPT], T[PPT], Tf[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gTv[PPT], S0[PPT], S1[PPT], S2[PPT];
+  float xs[PPT], T[PPT], Tf[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gTT[PPT], S0[PPT], S1[PPT], S2[PPT];
   int last[PPT];
   int my_max = 0;
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
     xs[p] = (float)(px0 + p) + 0.5f;
     T[p] = Tf[p] = 1.f;
-    gC0[p] = gC1[p] = gC2[p] = gTv[p] = 0.f;
+    gC0[p] = gC1[p] = gC2[p] = gTT[p] = 0.f;
     last[p] = 0;
     if (px0 + p < J.W && py < J.H) {
       const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p;
@@ -340,7 +340,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
       gC0[p] = grad_image[3 * pi];
       gC1[p] = grad_image[3 * pi + 1];
       gC2[p] = grad_image[3 * pi + 2];
-      gTv[p] = grad_t ? grad_t[pi] : 0.f;
+      gTT[p] = grad_t ? grad_t[pi] * Tf[p] : 0.f;  // dL/dT_final times T_final
     }
     S0[p] = P.bg[0] * Tf[p];
     S1[p] = P.bg[1] * Tf[p];
@@ -376,9 +376,10 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
       const float l01dy = __fmul_rn(a.w, dy);
       const float e2 = __fmul_rn(bb.x, dy);
       const float e2s = __fmul_rn(e2, e2);
-      float v[9];
-#pragma unroll
-      for (int m = 0; m < 9; ++m) v[m] = 0.f;
+      // per-strip sums: the geometric terms are gathered as sums over the
+      // strip's pixels of gq e1, gq dx, gq dx^2 and gq (dy and l11 dy are the
+      // same for the whole strip) and expanded once per record below
+      float s_e1 = 0.f, s_dx = 0.f, s_dx2 = 0.f, s_q = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
       bool any = false;
       const bool row_in = e2s <= bb.z;  // else q >= e2s > rho^2 for the whole strip
 #pragma unroll
@@ -395,29 +396,40 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
         const float iom = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 1 - alpha_max
         const float Tb = T[p] * iom;  // transmittance in front of this entry
         const float wgt = alpha * Tb;
-        v[6] += wgt * gC0[p];
-        v[7] += wgt * gC1[p];
-        v[8] += wgt * gC2[p];
+        v6 += wgt * gC0[p];
+        v7 += wgt * gC1[p];
+        v8 += wgt * gC2[p];
         const float ga = gC0[p] * (c.x * Tb - S0[p] * iom) + gC1[p] * (c.y * Tb - S1[p] * iom) +
-                         gC2[p] * (c.z * Tb - S2[p] * iom) - gTv[p] * Tf[p] * iom;
+                         gC2[p] * (c.z * Tb - S2[p] * iom) - gTT[p] * iom;
         S0[p] += c.x * wgt;
         S1[p] += c.y * wgt;
         S2[p] += c.z * wgt;
         T[p] = Tb;
         if (araw <= P.alpha_max) {
-          v[5] += f * ga;
+          v5 += f * ga;
           float gD = bb.y * ga * kern_df<KID>(xk) * P.inv_lambda;
           if (P.ags == 1) gD *= __expf(-D * D);
           else if (P.ags == 2) gD *= __expf(-xk * xk);
           const float gq = D > 0.f ? 0.5f * __fdividef(gD, D) : 0.f;
-          // A d = L^T (L d) = (l00 e1, l01 e1 + l11 e2)
-          v[0] += -2.f * gq * (a.z * e1);
-          v[1] += -2.f * gq * (a.w * e1 + bb.x * e2);
-          v[2] += gq * dx * dx;
-          v[3] += 2.f * gq * dx * dy;
-          v[4] += gq * dy * dy;
+          const float gdx = gq * dx;
+          s_e1 += gq * e1;
+          s_dx += gdx;
+          s_dx2 += gdx * dx;
+          s_q += gq;
         }
       }
+      // A d = L^T (L d) = (l00 e1, l01 e1 + l11 e2): the conic-space mean
+      // gradient and the conic-entry gradients (b counted once)
+      float v[9];
+      v[0] = -2.f * a.z * s_e1;
+      v[1] = -2.f * (a.w * s_e1 + bb.x * e2 * s_q);
+      v[2] = s_dx2;
+      v[3] = 2.f * dy * s_dx;
+      v[4] = dy * dy * s_q;
+      v[5] = v5;
+      v[6] = v6;
+      v[7] = v7;
+      v[8] = v8;
       const unsigned bal = __ballot_sync(FULL, any);
       if (bal == 0u) continue;
       if (__popc(bal) == 1) {

@@ -53,25 +53,35 @@ __global__ void __launch_bounds__(DUP_THREADS) dup_count_kernel(int64_t R, const
   rect_sorted[j] = rc;
 }
 
-// One block scans the warp counts (exclusive, in place), 16 consecutive
-// entries per thread and 16384 per round.
+// One block scans the counts (exclusive, in place) in rounds of 8192: a
+// coalesced load into shared memory, 8 consecutive entries per thread (two
+// 16-byte shared loads), a block scan of the thread sums, and a coalesced
+// store.
 __global__ void __launch_bounds__(1024) dup_scan_kernel(int64_t n, uint32_t* counts, int64_t cap, int64_t* n_keys,
                                                         int64_t* n_valid, int32_t* status) {
-  constexpr int PER = 16;
+  constexpr int PER = 8, ROUND = PER * 1024;
+  __shared__ __align__(16) uint32_t s_v[ROUND];
   __shared__ uint64_t s_warp[32];
   __shared__ uint64_t s_carry;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  for (int64_t b0 = 0; b0 < n; b0 += (int64_t)PER * 1024) {
-    const int64_t i0 = b0 + (int64_t)PER * threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_carry = 0;
+  for (int64_t b0 = 0; b0 < n; b0 += ROUND) {
+    const int m = (int)(n - b0 < ROUND ? n - b0 : ROUND);
+    for (int i = tid; i < ROUND; i += 1024) s_v[i] = i < m ? counts[b0 + i] : 0u;
+    __syncthreads();
     uint32_t v[PER];
+    const uint4* s4 = reinterpret_cast<const uint4*>(s_v + PER * tid);
+#pragma unroll
+    for (int q = 0; q < PER / 4; ++q) {
+      const uint4 u = s4[q];
+      v[4 * q] = u.x;
+      v[4 * q + 1] = u.y;
+      v[4 * q + 2] = u.z;
+      v[4 * q + 3] = u.w;
+    }
     uint64_t run = 0;
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      v[k] = i0 + k < n ? counts[i0 + k] : 0u;
-      run += v[k];
-    }
+    for (int k = 0; k < PER; ++k) run += v[k];
     uint64_t x = run;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -90,17 +100,23 @@ __global__ void __launch_bounds__(1024) dup_scan_kernel(int64_t n, uint32_t* cou
       s_warp[lane] = w;
     }
     __syncthreads();
-    uint64_t ex = x - run + (warp > 0 ? s_warp[warp - 1] : 0) + s_carry;
+    const uint64_t carry = s_carry;
+    uint64_t ex = x - run + (warp > 0 ? s_warp[warp - 1] : 0) + carry;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-      if (i0 + k < n) counts[i0 + k] = (uint32_t)ex;
-      ex += v[k];
+      const uint32_t c = v[k];
+      v[k] = (uint32_t)ex;
+      ex += c;
     }
+    uint4* d4 = reinterpret_cast<uint4*>(s_v + PER * tid);
+#pragma unroll
+    for (int q = 0; q < PER / 4; ++q) d4[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     __syncthreads();
-    if (threadIdx.x == 1023) s_carry = ex;
+    for (int i = tid; i < m; i += 1024) counts[b0 + i] = s_v[i];
+    if (tid == 1023) s_carry = ex;
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     const uint64_t K = s_carry;
     *n_keys = (int64_t)K;
     const bool fits = (int64_t)K <= cap;
@@ -114,26 +130,34 @@ __global__ void __launch_bounds__(1024) dup_scan_kernel(int64_t n, uint32_t* cou
 // tile is refuted and the depth is beyond its proposal.  In the count launch
 // of ENUM_KEPT a reached key beyond the proposal flags its tile in has_held.
 template <int MODE, bool COUNT>
-__device__ __forceinline__ bool cand_taken(const EnumArgs& A, const EnumRec& t, int tx, int ty, uint32_t key,
-                                           uint32_t& reached) {
-  if (!tile_reached(t, tx, ty, A.tile_w, A.tile_h)) return false;
+__device__ __forceinline__ bool cand_taken(const EnumArgs& A, const float4& g1, const float4& g2, uint32_t dk, int tx,
+                                           int ty, uint32_t key, uint32_t& reached) {
+  if (!tile_reached(g1, g2, tx, ty, A.tile_w, A.tile_h)) return false;
   if (MODE == ENUM_ALL) return true;
   ++reached;
   const uint32_t lim = __ldg(A.dstar_bits + key);
   if (MODE == ENUM_KEPT) {
-    const bool kept = t.dk <= lim;
+    const bool kept = dk <= lim;
     if (COUNT && !kept && !__ldg(A.has_held + key)) A.has_held[key] = 1;
     return kept;
   }
-  return A.refuted[key] && t.dk > lim;
+  return A.refuted[key] && dk > lim;
 }
 
-// Keys of ENUM_WARP_RECS depth-ordered records per warp (emit.cuh).  EMIT =
-// false writes each warp's count (and, in ENUM_KEPT, adds every reached key
-// to *key_total and flags tiles in has_held); EMIT = true writes the keys at
-// the warp's scanned offset and the tile-sort digit histograms.  ENUM_HELD
-// drops up front every record whose box holds no refuted tile (summed-area
-// table `sat`).
+constexpr uint32_t NO_STASH = 0xFFFFFFFFu;
+
+// Keys of ENUM_WARP_RECS depth-ordered records per warp (emit.cuh).
+//
+// Count launch (EMIT = false): each warp walks its candidates, counts the
+// taken keys (warp_counts) and, when its whole box-candidate count fits in
+// the stash (tmp_*, bump-allocated per warp), also writes them there,
+// compacted (warp_tbase; NO_STASH otherwise).  ENUM_KEPT also adds every
+// reached key to *key_total and flags tiles in has_held.
+// Emit launch (EMIT = true), after the counts are scanned into offsets: a
+// stashed warp copies its keys to its offset; any other warp walks its
+// candidates again and writes them.  Both gather the tile-sort digit
+// histograms.  ENUM_HELD drops up front every record whose box holds no
+// refuted tile (summed-area table `sat`).
 template <bool EMIT, int MODE>
 __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
   __shared__ EnumRec S[ENUM_WARPS][ENUM_WARP_RECS];
@@ -144,7 +168,10 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
   const unsigned lt = (1u << lane) - 1u;
   const int64_t gw = (int64_t)blockIdx.x * ENUM_WARPS + warp;
   if ((MODE == ENUM_HELD && *A.n_refuted == 0u) || (EMIT && *A.n_valid == 0)) {
-    if (!EMIT && lane == 0) A.warp_counts[gw] = 0u;
+    if (!EMIT && lane == 0) {
+      A.warp_counts[gw] = 0u;
+      A.warp_tbase[gw] = NO_STASH;
+    }
     return;  // block-uniform: nothing to do, or over capacity
   }
   for (int c = tid; c < A.cams.n; c += ENUM_THREADS)
@@ -152,88 +179,139 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
   if (EMIT)
     for (int i = tid; i < 3 * RADIX; i += ENUM_THREADS) (&s_hist[0][0])[i] = 0;
   __syncthreads();
-  // the warp's records with candidates, compacted, with their offsets
-  EnumRec* W = S[warp];
-  int n_nz = 0;
-  uint32_t total = 0;
-  const int sx = s_cam[0].tiles_x + 1;
+  uint64_t out = 0;
+  bool walk = true;
+  if (EMIT) {
+    out = A.out_base + (uint64_t)A.warp_counts[gw];
+    const uint32_t tb = A.warp_tbase[gw];
+    if (tb != NO_STASH) {  // copy the stashed keys
+      walk = false;
+      const uint64_t end = gw + 1 < A.n_warps ? A.out_base + (uint64_t)A.warp_counts[gw + 1]
+                                              : A.out_base + (uint64_t)*A.n_valid;
+      const uint32_t n = (uint32_t)(end - out);
+      // four 32-key chunks in flight per lane
+      for (uint32_t i0 = 0; i0 < n; i0 += 128) {
+        uint32_t k[4], v[4];
 #pragma unroll
-  for (int i = 0; i < ENUM_WARP_RECS / 32; ++i) {
-    const int64_t j = (int64_t)blockIdx.x * ENUM_BLOCK_RECS + warp * ENUM_WARP_RECS + i * 32 + lane;
-    uint2 rc = make_uint2(1u, 0u);
-    uint32_t r = 0, dk = DKEY_CULLED;
-    if (j < A.R) {
-      rc = A.rect_sorted[j];
-      r = A.order[j];
-      if (MODE != ENUM_ALL) dk = A.dkey_sorted[j];
-    }
-    uint32_t cnt = box_count(rc);
-    if (MODE == ENUM_HELD && cnt) {
-      const int x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF, y1 = rc.y >> 16;
-      const int* sat = A.sat;
-      if (sat[(y1 + 1) * sx + x1 + 1] - sat[y0 * sx + x1 + 1] - sat[(y1 + 1) * sx + x0] + sat[y0 * sx + x0] == 0)
-        cnt = 0u;
-    }
-    uint32_t x = cnt;
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t i = i0 + 32 * u + lane;
+          if (i < n) {
+            k[u] = A.tmp_keys[tb + i];
+            v[u] = A.tmp_vals[tb + i];
+          }
+        }
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(FULL, x, o);
-      if (lane >= o) x += u;
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t i = i0 + 32 * u + lane;
+          if (i < n) {
+            A.keys[out + i] = k[u];
+            A.vals[out + i] = v[u];
+            for (int p = 0; p < A.key_passes; ++p) atomicAdd(&s_hist[p][(k[u] >> (8 * p)) & 255u], 1u);
+          }
+        }
+      }
     }
-    const unsigned nz = __ballot_sync(FULL, cnt > 0);
-    if (cnt) {
-      EnumRec& t = W[n_nz + __popc(nz & lt)];
-      const CamLite cm = s_cam[A.cams.n > 1 ? r / (uint32_t)A.n_per_cam : 0u];
-      enum_rec(t, rc, r, dk, cm, A.rec);
-      t.off = total + x - cnt;
-    }
-    n_nz += __popc(nz);
-    total += __shfl_sync(FULL, x, 31);
   }
-  __syncwarp();
-  const uint64_t out = EMIT ? A.out_base + (uint64_t)A.warp_counts[gw] : 0u;
-  uint32_t kept = 0, reached = 0;
-  int sp = 0;  // record of the step's first candidate
-  for (uint32_t cb = 0; cb < total; cb += 32) {
-    // lane i marks where record sp + 1 + i starts, when inside this step;
-    // lane l's record is sp plus the number of marks at or below l
-    const int ns = sp + 1 + lane;
-    uint32_t mark = 0;
-    if (ns < n_nz) {
-      const uint32_t d = W[ns].off - cb;
-      if (d < 32u) mark = 1u << d;
-    }
-    const uint32_t M = __reduce_or_sync(FULL, mark);
-    const int sl = sp + __popc(M & ((2u << lane) - 1u));
-    const uint32_t e = cb + lane;
-    bool take = false;
-    uint32_t key = 0;
-    if (e < total) {
-      int tx, ty;
-      key = cand_key(W[sl], e - W[sl].off, tx, ty);
-      take = cand_taken<MODE, !EMIT>(A, W[sl], tx, ty, key, reached);
-    }
-    sp = __shfl_sync(FULL, sl, 31);
-    const unsigned bal = __ballot_sync(FULL, take);
-    if (EMIT && take) {
-      const uint64_t pos = out + kept + __popc(bal & lt);
-      A.keys[pos] = key;
-      A.vals[pos] = W[sl].r;
-      for (int p = 0; p < A.key_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
-    }
-    kept += __popc(bal);
-  }
-  if (!EMIT) {
-    if (MODE == ENUM_KEPT) {
+  if (walk) {
+    // the warp's records with candidates, compacted, with their offsets
+    EnumRec* W = S[warp];
+    int n_nz = 0;
+    uint32_t total = 0;
+    const int sx = s_cam[0].tiles_x + 1;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) reached += __shfl_xor_sync(FULL, reached, o);
+    for (int i = 0; i < ENUM_WARP_RECS / 32; ++i) {
+      const int64_t j = (int64_t)blockIdx.x * ENUM_BLOCK_RECS + warp * ENUM_WARP_RECS + i * 32 + lane;
+      uint2 rc = make_uint2(1u, 0u);
+      uint32_t r = 0, dk = DKEY_CULLED;
+      if (j < A.R) {
+        rc = A.rect_sorted[j];
+        r = A.order[j];
+        if (MODE != ENUM_ALL) dk = A.dkey_sorted[j];
+      }
+      uint32_t cnt = box_count(rc);
+      if (MODE == ENUM_HELD && cnt) {
+        const int x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF, y1 = rc.y >> 16;
+        const int* sat = A.sat;
+        if (sat[(y1 + 1) * sx + x1 + 1] - sat[y0 * sx + x1 + 1] - sat[(y1 + 1) * sx + x0] + sat[y0 * sx + x0] == 0)
+          cnt = 0u;
+      }
+      uint32_t x = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += u;
+      }
+      const unsigned nz = __ballot_sync(FULL, cnt > 0);
+      if (cnt) {
+        const CamLite cm = s_cam[A.cams.n > 1 ? r / (uint32_t)A.n_per_cam : 0u];
+        enum_rec(W[n_nz + __popc(nz & lt)], total + x - cnt, rc, r, dk, cm, A.rec);
+      }
+      n_nz += __popc(nz);
+      total += __shfl_sync(FULL, x, 31);
     }
-    if (lane == 0) {
-      A.warp_counts[gw] = kept;
-      if (MODE == ENUM_KEPT && reached) atomicAdd(A.key_total, (unsigned long long)reached);
+    __syncwarp();
+    // count launch: a stash region for every box candidate of the warp
+    uint32_t tb = NO_STASH;
+    if (!EMIT) {
+      if (lane == 0 && total > 0) {
+        const unsigned long long b = atomicAdd(A.tmp_ctr, (unsigned long long)total);
+        if (b + total <= (unsigned long long)A.tmp_cap) tb = (uint32_t)b;
+      }
+      tb = __shfl_sync(FULL, tb, 0);
     }
-    return;
+    uint32_t kept = 0, reached = 0;
+    int sp = 0;  // record of the step's first candidate
+    for (uint32_t cb = 0; cb < total; cb += 32) {
+      // lane i marks where record sp + 1 + i starts, when inside this step;
+      // lane l's record is sp plus the number of marks at or below l
+      const int ns = sp + 1 + lane;
+      uint32_t mark = 0;
+      if (ns < n_nz) {
+        const uint32_t d = W[ns].off - cb;
+        if (d < 32u) mark = 1u << d;
+      }
+      const uint32_t M = __reduce_or_sync(FULL, mark);
+      const int sl = sp + __popc(M & ((2u << lane) - 1u));
+      const uint32_t e = cb + lane;
+      bool take = false;
+      uint32_t key = 0, r = 0;
+      if (e < total) {
+        const uint4* q = reinterpret_cast<const uint4*>(&W[sl]);
+        const uint4 g0 = q[0], g3 = q[3];
+        const float4 g1 = reinterpret_cast<const float4*>(q)[1], g2 = reinterpret_cast<const float4*>(q)[2];
+        int tx, ty;
+        key = cand_key(g0, __uint_as_float(g3.z), e - g0.x, tx, ty);
+        take = cand_taken<MODE, !EMIT>(A, g1, g2, g3.y, tx, ty, key, reached);
+        r = g3.x;
+      }
+      sp = __shfl_sync(FULL, sl, 31);
+      const unsigned bal = __ballot_sync(FULL, take);
+      if (take) {
+        const uint32_t rank = kept + __popc(bal & lt);
+        if (EMIT) {
+          A.keys[out + rank] = key;
+          A.vals[out + rank] = r;
+          for (int p = 0; p < A.key_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
+        } else if (tb != NO_STASH) {
+          A.tmp_keys[tb + rank] = key;
+          A.tmp_vals[tb + rank] = r;
+        }
+      }
+      kept += __popc(bal);
+    }
+    if (!EMIT) {
+      if (MODE == ENUM_KEPT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) reached += __shfl_xor_sync(FULL, reached, o);
+      }
+      if (lane == 0) {
+        A.warp_counts[gw] = kept;
+        A.warp_tbase[gw] = tb;
+        if (MODE == ENUM_KEPT && reached) atomicAdd(A.key_total, (unsigned long long)reached);
+      }
+    }
   }
+  if (!EMIT) return;
   __syncthreads();
   for (int i = tid; i < A.key_passes * RADIX; i += ENUM_THREADS) {
     const uint32_t v = (&s_hist[0][0])[i];

@@ -77,7 +77,12 @@ struct EnumArgs {
   const uint8_t* refuted;         // [tiles] (ENUM_HELD)
   const int* sat;                 // summed-area table of refuted (ENUM_HELD)
   const unsigned* n_refuted;      // (ENUM_HELD)
-  uint32_t* warp_counts;          // [enum_warps(R)] taken keys per warp, then scanned offsets
+  uint32_t* warp_counts;          // [n_warps] taken keys per warp, then scanned offsets
+  uint32_t* warp_tbase;           // [n_warps] stash offset of each warp's keys (0xFFFFFFFF: none)
+  int64_t n_warps;                // enum_warps(R)
+  uint32_t *tmp_keys, *tmp_vals;  // stash of the count launch, tmp_cap entries
+  int64_t tmp_cap;
+  unsigned long long* tmp_ctr;    // stash bump allocator, zeroed before the count launch
   const int64_t* n_valid;         // total that fits the capacity (emit)
   uint64_t out_base;              // emit: first output position
   uint32_t *keys, *vals;          // emit outputs
