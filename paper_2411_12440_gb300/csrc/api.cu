@@ -502,7 +502,6 @@ struct LearnedWs {
   uint32_t *dk_a, *dv_a, *dk_b, *dv_b;
   uint2* rect;
   int* diff;
-  int32_t* tile_total;
   void* x16;
   float* y;
   uint32_t* dstar_bits;
@@ -539,7 +538,6 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
   w.dk_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
   w.dv_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
   w.rect = reinterpret_cast<uint2*>(take(8 * Rz));
-  w.tile_total = reinterpret_cast<int32_t*>(take(4 * tiles));
   w.x16 = take(2 * LS_MLP_IN * tiles);
   w.y = reinterpret_cast<float*>(take(4 * tiles));
   w.dstar_bits = reinterpret_cast<uint32_t*>(take(4 * tiles));
@@ -614,7 +612,7 @@ ls_status ls_tile_features(const void* proj, int64_t n_records, const ls_camera*
   const ParDev P = make_par(params);
   LS_TRY(cudaMemsetAsync(workspace, 0, ls_tile_features_workspace(cam, params), st));
   ProjCPtr pp = proj_cplanes(proj, n_records);
-  LS_TRY(launch_tile_hist(n_records, pp.rec, pp.foot, pp.dkey, T.c[0], P, workspace, st));
+  LS_TRY(launch_tile_hist(n_records, pp.rec, pp.foot, pp.dkey, T.c[0], P, workspace, true, st));
   LS_TRY(launch_features(workspace, T.c[0], P, features, tile_total, nullptr, st));
   return LS_OK;
 }
@@ -665,8 +663,8 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
     LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n, P, w.rect, st));
   }
   // per-tile features and the proposal
-  LS_TRY(launch_tile_hist(R, pp.rec, pp.foot, pp.dkey, C, P, w.diff, st));
-  LS_TRY(launch_features(w.diff, C, P, w.x16, w.tile_total, nullptr, st));
+  LS_TRY(launch_tile_hist(R, pp.rec, pp.foot, pp.dkey, C, P, w.diff, false, st));
+  LS_TRY(launch_features(w.diff, C, P, w.x16, nullptr, nullptr, st));
   if (mlp) LS_TRY(launch_mlp_forward(tiles, w.x16, mlp_dev(mlp), w.y, st));
   LS_TRY(launch_dstar(tiles, mlp ? w.y : nullptr, margin, dstar_in, w.dstar_bits, dstar_out, st));
   // kept keys: count per warp (and every key the ellipses reach), scan,

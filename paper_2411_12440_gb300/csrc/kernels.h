@@ -134,8 +134,9 @@ DepthBins make_depth_bins();
 // Scratch planes of the per-tile histograms (32 float coverage planes and one
 // int count plane of (tiles_x + 1) x (tiles_y + 1)), zeroed by the caller.
 size_t hist_planes_bytes(const CamDev& cam);
+// counts = false leaves out the plane of box counts (no tile totals wanted).
 cudaError_t launch_tile_hist(int64_t R, const float4* rec, const float4* foot, const uint32_t* dkey,
-                             const CamDev& cam, const ParDev& P, void* planes, cudaStream_t st);
+                             const CamDev& cam, const ParDev& P, void* planes, bool counts, cudaStream_t st);
 cudaError_t launch_features(void* planes, const CamDev& cam, const ParDev& P, void* x, int32_t* tile_total,
                             unsigned long long* key_total, cudaStream_t st);
 cudaError_t launch_dstar(int ntiles, const float* y, float margin, const float* dstar_in, uint32_t* bits,

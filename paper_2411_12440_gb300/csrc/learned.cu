@@ -43,10 +43,12 @@ __device__ __forceinline__ int depth_bin(float d, const DepthBins& B) {
 // count plane, and its expected coverage of a tile to its depth bin's plane:
 // o/3 (the mean of the linear profile over its support ellipse) times
 // min(1, ellipse area / box area).  Every record's count corners land on a
-// few thousand cells, so with PRIVATE the blocks are persistent and keep the
-// count plane in shared memory, adding it to the global one once at the end;
-// the mass corners spread over 32 planes and go to global memory directly.
-template <bool PRIVATE>
+// few thousand cells, so with COUNTS == HIST_PRIVATE the blocks are
+// persistent and keep the count plane in shared memory, adding it to the
+// global one once at the end; the mass corners spread over 32 planes and go
+// to global memory directly.  HIST_NONE leaves the count plane out.
+enum { HIST_NONE = 0, HIST_PRIVATE = 1, HIST_GLOBAL = 2 };
+template <int COUNTS>
 __global__ void __launch_bounds__(256) tile_hist_kernel(int64_t R, const float4* __restrict__ rec,
                                                         const float4* __restrict__ foot,
                                                         const uint32_t* __restrict__ dkey, const CamDev cam,
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(int64_t R, const float4*
   extern __shared__ int s_count[];
   const int sx = cam.tiles_x + 1, cells = sx * (cam.tiles_y + 1);
   int* cnt = count;
-  if (PRIVATE) {
+  if (COUNTS == HIST_PRIVATE) {
     for (int i = threadIdx.x; i < cells; i += blockDim.x) s_count[i] = 0;
     __syncthreads();
     cnt = s_count;
@@ -70,17 +72,19 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(int64_t R, const float4*
     const float ellipse = 3.14159265f * b.z / fmaxf(a.z * b.x, 1e-30f);
     const float box = (float)((tx1 - tx0 + 1) * (ty1 - ty0 + 1) * P.tile_w * P.tile_h);
     const float w = b.y * (1.f / 3.f) * fminf(1.f, ellipse / box);
-    atomicAdd(&cnt[ty0 * sx + tx0], 1);
-    atomicAdd(&cnt[ty0 * sx + tx1 + 1], -1);
-    atomicAdd(&cnt[(ty1 + 1) * sx + tx0], -1);
-    atomicAdd(&cnt[(ty1 + 1) * sx + tx1 + 1], 1);
+    if (COUNTS != HIST_NONE) {
+      atomicAdd(&cnt[ty0 * sx + tx0], 1);
+      atomicAdd(&cnt[ty0 * sx + tx1 + 1], -1);
+      atomicAdd(&cnt[(ty1 + 1) * sx + tx0], -1);
+      atomicAdd(&cnt[(ty1 + 1) * sx + tx1 + 1], 1);
+    }
     float* d = mass + (size_t)depth_bin(__uint_as_float(dk), bins) * cells;
     atomicAdd(&d[ty0 * sx + tx0], w);
     atomicAdd(&d[ty0 * sx + tx1 + 1], -w);
     atomicAdd(&d[(ty1 + 1) * sx + tx0], -w);
     atomicAdd(&d[(ty1 + 1) * sx + tx1 + 1], w);
   }
-  if (PRIVATE) {
+  if (COUNTS == HIST_PRIVATE) {
     __syncthreads();
     for (int i = threadIdx.x; i < cells; i += blockDim.x)
       if (s_count[i]) atomicAdd(&count[i], s_count[i]);
@@ -159,9 +163,11 @@ __global__ void __launch_bounds__(256) features_kernel(const float* __restrict__
   for (int i = 0; i < 3; ++i)
     row[NBINS + i] = __float2half_rn(cam.R[i] * c0 + cam.R[3 + i] * c1 + cam.R[6 + i] * c2);
   for (int i = NBINS + 3; i < LS_MLP_IN; ++i) row[i] = __float2half_rn(0.f);
-  const int total = count[ty * sx + tx];
-  tile_total[t] = total;
-  if (key_total) atomicAdd(key_total, (unsigned long long)total);
+  if (tile_total) {
+    const int total = count[ty * sx + tx];
+    tile_total[t] = total;
+    if (key_total) atomicAdd(key_total, (unsigned long long)total);
+  }
 }
 
 // Proposed depth per tile as comparable bits: exp(y + margin) from the MLP,
@@ -216,23 +222,28 @@ size_t hist_planes_bytes(const CamDev& cam) {
 }
 
 cudaError_t launch_tile_hist(int64_t R, const float4* rec, const float4* foot, const uint32_t* dkey,
-                             const CamDev& cam, const ParDev& P, void* planes, cudaStream_t st) {
+                             const CamDev& cam, const ParDev& P, void* planes, bool counts, cudaStream_t st) {
   if (R == 0) return cudaSuccess;
   float* mass = static_cast<float*>(planes);
   int* count = reinterpret_cast<int*>(mass + (size_t)NBINS * (cam.tiles_x + 1) * (cam.tiles_y + 1));
   const size_t plane = sizeof(int) * (size_t)(cam.tiles_x + 1) * (cam.tiles_y + 1);
-  if (plane <= 96 * 1024) {
+  if (!counts) {
+    tile_hist_kernel<HIST_NONE><<<ceil_div(R, 256), 256, 0, st>>>(R, rec, foot, dkey, cam, P, make_depth_bins(),
+                                                                  count, mass);
+  } else if (plane <= 96 * 1024) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess && plane > 48 * 1024)
-      e = cudaFuncSetAttribute(tile_hist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane);
+      e = cudaFuncSetAttribute(tile_hist_kernel<HIST_PRIVATE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)plane);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(R, 256), (int64_t)sms * 4);
-    tile_hist_kernel<true><<<grid, 256, plane, st>>>(R, rec, foot, dkey, cam, P, make_depth_bins(), count, mass);
+    tile_hist_kernel<HIST_PRIVATE><<<grid, 256, plane, st>>>(R, rec, foot, dkey, cam, P, make_depth_bins(), count,
+                                                             mass);
   } else {
-    tile_hist_kernel<false><<<ceil_div(R, 256), 256, 0, st>>>(R, rec, foot, dkey, cam, P, make_depth_bins(), count,
-                                                              mass);
+    tile_hist_kernel<HIST_GLOBAL><<<ceil_div(R, 256), 256, 0, st>>>(R, rec, foot, dkey, cam, P, make_depth_bins(),
+                                                                    count, mass);
   }
   return cudaGetLastError();
 }
@@ -241,7 +252,8 @@ cudaError_t launch_features(void* planes, const CamDev& cam, const ParDev& P, vo
                             unsigned long long* key_total, cudaStream_t st) {
   float* mass = static_cast<float*>(planes);
   int* count = reinterpret_cast<int*>(mass + (size_t)NBINS * (cam.tiles_x + 1) * (cam.tiles_y + 1));
-  hist_prefix_kernel<<<NBINS + 1, 256, 0, st>>>(mass, count, cam.tiles_x + 1, cam.tiles_y + 1);
+  // the count plane is prefixed only when its totals are wanted
+  hist_prefix_kernel<<<tile_total ? NBINS + 1 : NBINS, 256, 0, st>>>(mass, count, cam.tiles_x + 1, cam.tiles_y + 1);
   const int ntiles = cam.tiles_x * cam.tiles_y;
   features_kernel<<<ceil_div(ntiles, 256), 256, 0, st>>>(mass, count, cam, P, static_cast<__half*>(x), tile_total,
                                                         key_total);
