@@ -144,7 +144,7 @@ DupWs dup_layout(char* base, int64_t R, int64_t cap, int key_passes) {
   w.v_alt = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.zero_begin = off;
   w.tmp_ctr = reinterpret_cast<unsigned long long*>(take(8));
-  w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4));
+  w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4, SORT_ITEMS_SMALL));
   w.tile_scratch = take(sort_scratch_bytes((int64_t)Cz, key_passes));
   w.zero_bytes = off - w.zero_begin;
   w.total = off;
@@ -213,6 +213,7 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
   if (n_records > 0 && !proj) return LS_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(workspace) % 256) return LS_ERR_INVALID_ARG;
   const int kp = key_passes_for(total_tiles);
+  const TileDigits td = tile_digits(total_tiles);
   DupWs w = dup_layout(static_cast<char*>(workspace), n_records, key_capacity, kp);
   if (ws_bytes < w.total) return LS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -224,14 +225,14 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
   LS_TRY(cudaMemsetAsync(static_cast<char*>(workspace) + w.zero_begin, 0, w.zero_bytes, st));
   // depth sort of the records: key = binary32 depth bits (0xFFFFFFFF when
   // culled), value = record id; four 8-bit passes, the last lands in (dk_a, dv_a)
-  SortScratch ds = sort_scratch_carve(w.depth_scratch, R > 0 ? R : 1, 4);
+  SortScratch ds = sort_scratch_carve(w.depth_scratch, R > 0 ? R : 1, 4, SORT_ITEMS_SMALL);
   if (R > 0) {
     LS_TRY(launch_radix_hist(pp.dkey, nullptr, R, 0, 4, ds.hist, st));
     LS_TRY(launch_radix_scan(ds.hist, 4, st));
-    LS_TRY(launch_onesweep_pass(pp.dkey, nullptr, w.dk_b, w.dv_b, nullptr, R, R, 0, 0, ds, nullptr, status_dev, st));
-    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 1, ds, nullptr, status_dev, st));
-    LS_TRY(launch_onesweep_pass(w.dk_a, w.dv_a, w.dk_b, w.dv_b, nullptr, R, R, 0, 2, ds, nullptr, status_dev, st));
-    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 3, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(pp.dkey, nullptr, w.dk_b, w.dv_b, nullptr, R, R, 0, 8, 0, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 8, 8, 1, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_a, w.dv_a, w.dk_b, w.dv_b, nullptr, R, R, 16, 8, 2, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 24, 8, 3, ds, nullptr, status_dev, st));
     LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n_per_cam, P, w.rect, st));
   }
   // keys of the tiles each support ellipse reaches: count per warp (and
@@ -261,6 +262,10 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
   ea.tmp_ctr = w.tmp_ctr;
   ea.n_valid = w.n_valid;
   ea.key_passes = kp;
+  for (int p = 0; p < kp; ++p) {
+    ea.dshift[p] = td.shift[p];
+    ea.dmask[p] = (1u << td.bits[p]) - 1u;
+  }
   LS_TRY(launch_enum_keys(false, ENUM_ALL, ea, st));
   LS_TRY(launch_dup_scan(enum_warps(R), w.warp_counts, key_capacity, n_keys_dev, w.n_valid, status_dev, st));
   SortScratch ts = sort_scratch_carve(w.tile_scratch, key_capacity > 0 ? key_capacity : 1, kp);
@@ -273,7 +278,7 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
     LS_TRY(launch_enum_keys(true, ENUM_ALL, ea, st));
     LS_TRY(launch_radix_scan(ts.hist, kp, st));
     for (int p = 0; p < kp; ++p) {
-      LS_TRY(launch_onesweep_pass(ek, ev, ok, ov, w.n_valid, 0, key_capacity, 0, p, ts,
+      LS_TRY(launch_onesweep_pass(ek, ev, ok, ov, w.n_valid, 0, key_capacity, td.shift[p], td.bits[p], p, ts,
                                   p == kp - 1 ? tile_ranges : nullptr, status_dev, st));
       std::swap(ek, ok);
       std::swap(ev, ov);
@@ -557,7 +562,7 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
   w.h_ranges = reinterpret_cast<int32_t*>(take(8 * tiles));
   // cleared before every call
   w.zero_begin = off;
-  w.diff = reinterpret_cast<int*>(take(4 * 33 * (size_t)(tiles_x + 1) * (tiles_y + 1)));
+  w.diff = reinterpret_cast<int*>(take((32 * 8 + 4) * (size_t)(tiles_x + 1) * (tiles_y + 1)));  // coverage planes
   w.refuted = reinterpret_cast<uint8_t*>(take(tiles));
   w.has_held = reinterpret_cast<uint8_t*>(take(tiles));
   w.tmp_ctr_kept = reinterpret_cast<unsigned long long*>(take(8));
@@ -568,7 +573,7 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
   w.n_held_valid = reinterpret_cast<int64_t*>(take(8));
   w.n_refuted = reinterpret_cast<unsigned*>(take(4));
   w.key_total = reinterpret_cast<unsigned long long*>(take(8));
-  w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4));
+  w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4, SORT_ITEMS_SMALL));
   w.kept_scratch = take(sort_scratch_bytes((int64_t)Cz, kp));
   w.held_scratch = take(sort_scratch_bytes((int64_t)Cz, kp));
   w.zero_bytes = off - w.zero_begin;
@@ -580,9 +585,11 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
 // (keys, vals); the last pass records the ranges.
 ls_status tile_sort(uint32_t* ek, uint32_t* ev, uint32_t* ok, uint32_t* ov, const int64_t* n_dev, int64_t cap, int kp,
                     const SortScratch& ss, int32_t* ranges, int tiles, int32_t* status, cudaStream_t st) {
+  const TileDigits td = tile_digits(tiles);
   LS_TRY(launch_radix_scan(ss.hist, kp, st));
   for (int p = 0; p < kp; ++p) {
-    LS_TRY(launch_onesweep_pass(ek, ev, ok, ov, n_dev, 0, cap, 0, p, ss, p == kp - 1 ? ranges : nullptr, status, st));
+    LS_TRY(launch_onesweep_pass(ek, ev, ok, ov, n_dev, 0, cap, td.shift[p], td.bits[p], p, ss,
+                                p == kp - 1 ? ranges : nullptr, status, st));
     std::swap(ek, ok);
     std::swap(ev, ov);
   }
@@ -642,6 +649,7 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
     return LS_ERR_INVALID_ARG;
   const CamDev& C = T.c[0];
   const int tiles = (int)tiles64, kp = key_passes_for(tiles64);
+  const TileDigits td = tile_digits(tiles64);
   const int64_t R = n;
   LearnedWs w = learned_layout(static_cast<char*>(workspace), R, key_capacity, C.tiles_x, C.tiles_y, kp);
   if (ws_bytes < w.total) return LS_ERR_INVALID_ARG;
@@ -653,13 +661,13 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   // projection and depth order (as the plain path)
   if (R > 0) {
     LS_TRY(launch_project_fwd(n, means, scales, quats, opacities, sh, T, P, pw, nullptr, st));
-    SortScratch ds = sort_scratch_carve(w.depth_scratch, R, 4);
+    SortScratch ds = sort_scratch_carve(w.depth_scratch, R, 4, SORT_ITEMS_SMALL);
     LS_TRY(launch_radix_hist(pp.dkey, nullptr, R, 0, 4, ds.hist, st));
     LS_TRY(launch_radix_scan(ds.hist, 4, st));
-    LS_TRY(launch_onesweep_pass(pp.dkey, nullptr, w.dk_b, w.dv_b, nullptr, R, R, 0, 0, ds, nullptr, status_dev, st));
-    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 1, ds, nullptr, status_dev, st));
-    LS_TRY(launch_onesweep_pass(w.dk_a, w.dv_a, w.dk_b, w.dv_b, nullptr, R, R, 0, 2, ds, nullptr, status_dev, st));
-    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 0, 3, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(pp.dkey, nullptr, w.dk_b, w.dv_b, nullptr, R, R, 0, 8, 0, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 8, 8, 1, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_a, w.dv_a, w.dk_b, w.dv_b, nullptr, R, R, 16, 8, 2, ds, nullptr, status_dev, st));
+    LS_TRY(launch_onesweep_pass(w.dk_b, w.dv_b, w.dk_a, w.dv_a, nullptr, R, R, 24, 8, 3, ds, nullptr, status_dev, st));
     LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n, P, w.rect, st));
   }
   // per-tile features and the proposal
@@ -690,6 +698,10 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   ea.sat = w.sat;
   ea.n_refuted = w.n_refuted;
   ea.key_passes = kp;
+  for (int p = 0; p < kp; ++p) {
+    ea.dshift[p] = td.shift[p];
+    ea.dmask[p] = (1u << td.bits[p]) - 1u;
+  }
   ea.key_total = w.key_total;
   ea.has_held = w.has_held;
   ea.warp_counts = w.wc_kept;

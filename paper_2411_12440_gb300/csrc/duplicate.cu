@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
           if (i < n) {
             A.keys[out + i] = k[u];
             A.vals[out + i] = v[u];
-            for (int p = 0; p < A.key_passes; ++p) atomicAdd(&s_hist[p][(k[u] >> (8 * p)) & 255u], 1u);
+            for (int p = 0; p < A.key_passes; ++p) atomicAdd(&s_hist[p][(k[u] >> A.dshift[p]) & A.dmask[p]], 1u);
           }
         }
       }
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
         if (EMIT) {
           A.keys[out + rank] = key;
           A.vals[out + rank] = r;
-          for (int p = 0; p < A.key_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
+          for (int p = 0; p < A.key_passes; ++p) atomicAdd(&s_hist[p][(key >> A.dshift[p]) & A.dmask[p]], 1u);
         } else if (tb != NO_STASH) {
           A.tmp_keys[tb + rank] = key;
           A.tmp_vals[tb + rank] = r;

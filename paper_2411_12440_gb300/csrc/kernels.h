@@ -19,8 +19,12 @@ cudaError_t launch_project_bwd(int n, const float* means, const float* scales, c
 
 // ---- onesweep radix sort (sort.cu)
 constexpr int SORT_THREADS = 256;
+// Keys per thread of a partition: the key sorts run 15 (3840-key
+// partitions); the record-depth sort, a few million keys, runs 8 so that its
+// partitions fill the GPU in more than one wave.
 constexpr int SORT_ITEMS = 15;
-constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per partition
+constexpr int SORT_ITEMS_SMALL = 8;
+constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per partition (largest)
 constexpr int RADIX = 256;
 
 // Scratch of one sort of up to `cap` keys over `passes` 8-bit digits.
@@ -29,25 +33,47 @@ struct SortScratch {
   uint32_t* part_ctr;  // [passes] partition tickets
   uint64_t* lookback;  // [passes][parts][RADIX]
   int64_t parts;
+  int items;           // keys per thread of a partition
 };
-size_t sort_scratch_bytes(int64_t cap, int passes);
-SortScratch sort_scratch_carve(void* base, int64_t cap, int passes);
+size_t sort_scratch_bytes(int64_t cap, int passes, int items = SORT_ITEMS);
+SortScratch sort_scratch_carve(void* base, int64_t cap, int passes, int items = SORT_ITEMS);
 
 // Digit histograms of all passes in one read (skipped when the caller has
 // filled `hist` itself); then the exclusive scans.
 cudaError_t launch_radix_hist(const uint32_t* keys, const int64_t* n_dev, int64_t n_host, int begin_bit,
                               int passes, uint32_t* hist, cudaStream_t st);
 cudaError_t launch_radix_scan(uint32_t* hist, int passes, cudaStream_t st);
-// One onesweep pass (digit `pass`, bits [begin_bit + 8 pass, +8)).
+// One onesweep pass over digit (key >> shift) & (2^bits - 1), bits in 4..8,
+// using the scratch of pass index `pass`.
 // vals_in == nullptr means the identity values 0..n-1.  n is read from
 // n_dev when not null, else n_host; the grid covers `cap` keys.
 // ranges != nullptr on the last pass of a tile sort: the pass also records
 // each tile's [start, end) (prefilled with 0xFF bytes, finished by
 // launch_ranges_fixup).
 cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
-                                 uint32_t* vals_out, const int64_t* n_dev, int64_t n_host, int64_t cap,
-                                 int begin_bit, int pass, const SortScratch& s, int32_t* ranges, int32_t* status,
+                                 uint32_t* vals_out, const int64_t* n_dev, int64_t n_host, int64_t cap, int shift,
+                                 int bits, int pass, const SortScratch& s, int32_t* ranges, int32_t* status,
                                  cudaStream_t st);
+// Digits of a tile sort: the bits of the largest tile id split evenly over
+// ceil(bits / 8) passes (the earlier passes take the remainder).
+struct TileDigits {
+  int passes;
+  int shift[3], bits[3];
+};
+inline TileDigits tile_digits(int64_t total_tiles) {
+  int nb = 1;
+  while ((1ll << nb) < total_tiles) ++nb;
+  TileDigits d{};
+  d.passes = (nb + 7) / 8;
+  int at = 0;
+  for (int p = 0; p < d.passes; ++p) {
+    const int b = (nb - at + (d.passes - p) - 1) / (d.passes - p);
+    d.shift[p] = at;
+    d.bits[p] = b < 4 ? 4 : b;
+    at += b;
+  }
+  return d;
+}
 cudaError_t launch_ranges_fixup(int32_t* ranges, int total_tiles, cudaStream_t st);
 
 // ---- duplication and tile ranges (duplicate.cu)
@@ -87,6 +113,8 @@ struct EnumArgs {
   uint64_t out_base;              // emit: first output position
   uint32_t *keys, *vals;          // emit outputs
   int key_passes;
+  int dshift[3];                  // digit p of a key: (key >> dshift[p]) & dmask[p]
+  uint32_t dmask[3];
   uint32_t* tile_hist;            // [key_passes][RADIX] digit counts (emit)
   unsigned long long* key_total;  // ENUM_KEPT count launch: all keys reached
   uint8_t* has_held;              // ENUM_KEPT count launch: [tiles] set for tiles with keys beyond the proposal

@@ -1,5 +1,7 @@
-// a3: onesweep LSD radix sort of (uint32 key, uint32 value) pairs with 8-bit
-// digits (single-pass prefix by decoupled look-back).  Stable, so sorting the
+// a3: onesweep LSD radix sort of (uint32 key, uint32 value) pairs with digits
+// of up to 8 bits (single-pass prefix by decoupled look-back); the tile sort
+// splits the tile-id bits evenly over its passes (13 bits: 7 + 6), so each
+// pass ranks with as few ballots and digits as the keys need.  Stable, so sorting the
 // duplication output by tile id keeps each tile's entries in the depth order
 // they were emitted in: the front-to-back order of Sec. 3.1 Eq. 6.
 //
@@ -88,10 +90,11 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Dynamic shared memory of one onesweep block.
+template <int PART>
 struct OnesweepSmem {
-  uint32_t keys[SORT_PART];      // keys in block-sorted order
-  uint32_t vin[SORT_PART];       // the partition's values in input order (cp.async)
-  uint16_t src[SORT_PART];       // input position of the key at each sorted slot
+  uint32_t keys[PART];           // keys in block-sorted order
+  uint32_t vin[PART];            // the partition's values in input order (cp.async)
+  uint16_t src[PART];            // input position of the key at each sorted slot
   uint32_t whist[SORT_WARPS][RADIX];
   uint32_t local[RADIX];
   uint32_t glob[RADIX];
@@ -99,13 +102,18 @@ struct OnesweepSmem {
   uint32_t part;
 };
 
+// BITS: digit width of the pass (<= 8); digits are (key >> shift) & (2^BITS - 1).
+// ITEMS: keys per thread; a partition holds SORT_THREADS * ITEMS keys.
+template <int BITS, int ITEMS>
 __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const int64_t* n_dev, int64_t n_host, int shift,
     const uint32_t* __restrict__ digit_base, uint64_t* lookback, uint32_t* part_ctr, uint2* ranges,
     int32_t* status) {
+  constexpr uint32_t MASK = (1u << BITS) - 1u;
+  constexpr int PART = SORT_THREADS * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  OnesweepSmem& S = *reinterpret_cast<OnesweepSmem*>(smem_raw);
+  OnesweepSmem<PART>& S = *reinterpret_cast<OnesweepSmem<PART>*>(smem_raw);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&S.whist[0][0])[i] = 0;
@@ -113,9 +121,9 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
   __syncthreads();
   const int64_t n = n_dev ? *n_dev : n_host;
   const uint32_t part = S.part;
-  const int64_t base = (int64_t)part * SORT_PART;
+  const int64_t base = (int64_t)part * PART;
   if (base >= n) return;  // block-uniform
-  const int n_in = (int)(n - base < SORT_PART ? n - base : SORT_PART);
+  const int n_in = (int)(n - base < PART ? n - base : PART);
 
   // values: asynchronous copy into shared memory, in flight during ranking
   if (vals_in) {
@@ -123,26 +131,26 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
   // keys: warp-striped, warp w holds positions w*32*ITEMS + i*32 + lane
-  const int wofs = warp * 32 * SORT_ITEMS;
-  uint32_t k[SORT_ITEMS];
+  const int wofs = warp * 32 * ITEMS;
+  uint32_t k[ITEMS];
 #pragma unroll
-  for (int i = 0; i < SORT_ITEMS; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const int li = wofs + i * 32 + lane;
     k[i] = li < n_in ? keys_in[base + li] : 0xFFFFFFFFu;
   }
   // rank inside the warp: peers with the same digit from 8 ballots; items are
   // visited in position order, so ranks are stable.  Ranks fit 16 bits.
-  uint32_t rk[(SORT_ITEMS + 1) / 2];
+  uint32_t rk[(ITEMS + 1) / 2];
 #pragma unroll
-  for (int i = 0; i < (SORT_ITEMS + 1) / 2; ++i) rk[i] = 0;
+  for (int i = 0; i < (ITEMS + 1) / 2; ++i) rk[i] = 0;
   const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-  for (int i = 0; i < SORT_ITEMS; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const bool valid = wofs + i * 32 + lane < n_in;
-    const uint32_t d = (k[i] >> shift) & 255u;
+    const uint32_t d = (k[i] >> shift) & MASK;
     uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
+    for (int b = 0; b < BITS; ++b) {
       const uint32_t bit = (d >> b) & 1u;
       const uint32_t bal = __ballot_sync(0xffffffffu, bit);
       peers &= bit ? bal : ~bal;
@@ -166,11 +174,12 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
       run += c;
     }
     uint64_t* my = lookback + (size_t)part * RADIX + d;
-    st_relaxed_u64(my, (part == 0 ? LB_INC : LB_AGG) | (uint64_t)run);
+    const bool used = d <= (int)MASK;  // digits beyond the pass's width never occur
+    if (used) st_relaxed_u64(my, (part == 0 ? LB_INC : LB_AGG) | (uint64_t)run);
     const uint32_t incl = block_incl_scan(run, S.warp);
     S.local[d] = incl - run;
     uint64_t prefix = 0;
-    if (part > 0) {
+    if (used && part > 0) {
       int64_t p = (int64_t)part - 1;
       int spins = 0;
       while (p >= 0) {
@@ -194,10 +203,10 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
 
   // stage the keys (and where each came from) in block-sorted order
 #pragma unroll
-  for (int i = 0; i < SORT_ITEMS; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const int li = wofs + i * 32 + lane;
     if (li < n_in) {
-      const uint32_t d = (k[i] >> shift) & 255u;
+      const uint32_t d = (k[i] >> shift) & MASK;
       const uint32_t pos = S.local[d] + S.whist[warp][d] + ((rk[i / 2] >> (16 * (i & 1))) & 0xFFFFu);
       S.keys[pos] = k[i];
       S.src[pos] = (uint16_t)li;
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
   // digit runs go to consecutive global positions
   for (int s = tid; s < n_in; s += SORT_THREADS) {
     const uint32_t key = S.keys[s];
-    const uint32_t dst = S.glob[(key >> shift) & 255u] + (uint32_t)s;
+    const uint32_t dst = S.glob[(key >> shift) & MASK] + (uint32_t)s;
     if (dst < (uint64_t)n) {
       keys_out[dst] = key;
       vals_out[dst] = vals_in ? S.vin[S.src[s]] : (uint32_t)(base + S.src[s]);
@@ -235,15 +244,18 @@ inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
-size_t sort_scratch_bytes(int64_t cap, int passes) {
-  int64_t parts = cap > 0 ? (cap + SORT_PART - 1) / SORT_PART : 1;
+size_t sort_scratch_bytes(int64_t cap, int passes, int items) {
+  const int64_t part = (int64_t)SORT_THREADS * items;
+  int64_t parts = cap > 0 ? (cap + part - 1) / part : 1;
   return al256((size_t)passes * RADIX * 4) + al256((size_t)passes * 4) +
          al256((size_t)passes * parts * RADIX * 8);
 }
 
-SortScratch sort_scratch_carve(void* base, int64_t cap, int passes) {
+SortScratch sort_scratch_carve(void* base, int64_t cap, int passes, int items) {
   SortScratch s;
-  s.parts = cap > 0 ? (cap + SORT_PART - 1) / SORT_PART : 1;
+  const int64_t part = (int64_t)SORT_THREADS * items;
+  s.items = items;
+  s.parts = cap > 0 ? (cap + part - 1) / part : 1;
   char* p = static_cast<char*>(base);
   s.hist = reinterpret_cast<uint32_t*>(p);
   p += al256((size_t)passes * RADIX * 4);
@@ -265,27 +277,45 @@ cudaError_t launch_radix_scan(uint32_t* hist, int passes, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
-                                 uint32_t* vals_out, const int64_t* n_dev, int64_t n_host, int64_t cap,
-                                 int begin_bit, int pass, const SortScratch& s, int32_t* ranges, int32_t* status,
-                                 cudaStream_t st) {
+template <int BITS, int ITEMS>
+static cudaError_t onesweep_launch(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                   uint32_t* vals_out, const int64_t* n_dev, int64_t n_host, int64_t cap, int shift,
+                                   int pass, const SortScratch& s, int32_t* ranges, int32_t* status, cudaStream_t st) {
   // the dynamic shared memory limit is a per-device attribute of the kernel
   static bool attr_set[64] = {false};
-  const size_t sm = sizeof(OnesweepSmem);
+  constexpr int PART = SORT_THREADS * ITEMS;
+  const size_t sm = sizeof(OnesweepSmem<PART>);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaFuncSetAttribute(onesweep_kernel<BITS, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  unsigned grid = ceil_div(cap > 0 ? cap : 1, SORT_PART);
-  onesweep_kernel<<<grid, SORT_THREADS, sm, st>>>(keys_in, vals_in, keys_out, vals_out, n_dev, n_host,
-                                                  begin_bit + 8 * pass, s.hist + (size_t)pass * RADIX,
-                                                  s.lookback + (size_t)pass * s.parts * RADIX, s.part_ctr + pass,
-                                                  reinterpret_cast<uint2*>(ranges), status);
+  unsigned grid = ceil_div(cap > 0 ? cap : 1, PART);
+  onesweep_kernel<BITS, ITEMS><<<grid, SORT_THREADS, sm, st>>>(
+      keys_in, vals_in, keys_out, vals_out, n_dev, n_host, shift, s.hist + (size_t)pass * RADIX,
+      s.lookback + (size_t)pass * s.parts * RADIX, s.part_ctr + pass, reinterpret_cast<uint2*>(ranges), status);
   return cudaGetLastError();
+}
+
+cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                 uint32_t* vals_out, const int64_t* n_dev, int64_t n_host, int64_t cap, int shift,
+                                 int bits, int pass, const SortScratch& s, int32_t* ranges, int32_t* status,
+                                 cudaStream_t st) {
+#define LS_OS(B, I)                                                                                        \
+  onesweep_launch<B, I>(keys_in, vals_in, keys_out, vals_out, n_dev, n_host, cap, shift, pass, s, ranges, status, \
+                        st)
+  if (s.items == SORT_ITEMS_SMALL) return LS_OS(8, SORT_ITEMS_SMALL);  // depth sort: full bytes
+  switch (bits) {
+    case 4: return LS_OS(4, SORT_ITEMS);
+    case 5: return LS_OS(5, SORT_ITEMS);
+    case 6: return LS_OS(6, SORT_ITEMS);
+    case 7: return LS_OS(7, SORT_ITEMS);
+    default: return LS_OS(8, SORT_ITEMS);
+  }
+#undef LS_OS
 }
 
 cudaError_t launch_ranges_fixup(int32_t* ranges, int total_tiles, cudaStream_t st) {

@@ -162,14 +162,14 @@ def test_trained_network_gains_over_the_method_without_it():
     views = dict(w_range=(400, 640), h_range=(300, 480))
     train_scenes = [raster.Splats.from_scene(scenes.cluster_scene(1_200_000, 100 + k, 3)) for k in range(3)]
     xs, ys = [], []
-    for i in range(60):
+    for i in range(120):
         cam = scenes.ring_cameras(1, 1000 + i, **views)[0]
         x, y = tile_examples(rz_lab, train_scenes[i % 3], cam)
         xs.append(x)
         ys.append(y)
     x, y = torch.cat(xs), torch.cat(ys)
     net = TerminationMLP(seed=0)
-    losses = train(net, x, y, steps=1500, batch=16384, lr=2e-3, under_weight=1.0, log_every=500)
+    losses = train(net, x, y, steps=3000, batch=16384, lr=2e-3, under_weight=2.0, log_every=1000)
     assert losses[-1][1] < losses[0][1]
     tune_views = [(train_scenes[k % 3], scenes.ring_cameras(1, 1000 + k, **views)[0]) for k in range(3)]
     finite = torch.exp(y[y < math.log(64.0) - 1e-3]).float()
@@ -182,11 +182,11 @@ def test_trained_network_gains_over_the_method_without_it():
             s += _sorted_keys(lr, t_thr=t_thr, **kw_fn(lr))[0]
         return s
 
-    margin = min((0.0, 0.1, 0.25, 0.4), key=lambda m: cost(lambda lr: dict(mlp=net, margin=m)))
+    margin = min((0.0, 0.2, 0.4, 0.6, 0.8), key=lambda m: cost(lambda lr: dict(mlp=net, margin=m)))
     const = min(qs, key=lambda c: cost(lambda lr: dict(dstar_in=torch.full((lr.tiles,), c, device="cuda"))))
     test_scene = raster.Splats.from_scene(scenes.cluster_scene(1_200_000, 777, 3))
     tot = dict(mlp=0, const=0, all=0)
-    for i in range(4):
+    for i in range(6):
         cam = scenes.ring_cameras(1, 5000 + i, w_range=(512, 512), h_range=(384, 384))[0]
         img0, _, _ = rz.forward(test_scene, cam)
         lr = LearnedRenderer(test_scene, cam, P)
@@ -197,5 +197,6 @@ def test_trained_network_gains_over_the_method_without_it():
             tot[name] += k
             mse = float(((lr.image - img0) ** 2).mean().item())
             assert mse == 0.0 or -10 * math.log10(mse) >= 50.0
+    print("keys sorted over the held-out views:", tot, "margin", margin, "depth", const)
     assert tot["mlp"] < 0.75 * tot["all"], tot
     assert tot["mlp"] < tot["const"], tot
