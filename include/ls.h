@@ -112,11 +112,14 @@ ls_status ls_project(int32_t n, const float* means, const float* scales, const f
 size_t ls_duplicate_sort_workspace(int64_t n_records, int64_t key_capacity, int32_t total_tiles);
 
 /* a2+a3: duplication of every visible record into the tiles of its support
- * box that its support ellipse D^2 <= rho^2 reaches (minimum of D^2 over the
- * rectangle of the tile's pixel centres, tested in binary32 with a 2 % margin,
- * so every pair the blend can composite is listed), and a stable radix sort
- * into front-to-back order per tile (compositing order of Sec. 3.1 Eq. 6,
- * kept "without alteration", Sec. 3.2).  K is at most the sum of the
+ * box that its support ellipse reaches, and a stable radix sort into
+ * front-to-back order per tile (compositing order of Sec. 3.1 Eq. 6, kept
+ * "without alteration", Sec. 3.2).  Reach rule, binary32 with every operation
+ * rounded once: per box row, the ellipse D^2 <= 1.02 rho^2 + 1e-3 cut by the
+ * band of the row's pixel-centre heights has an x-extent (from its left and
+ * right boundary points), and the tiles whose pixel-centre columns meet it
+ * (0.01 px slack) are listed; boxes of at most 2 tiles are listed whole.
+ * Every pair the blend can composite is listed.  K is at most the sum of the
  * tile_counts of ls_project (the box tiles), which therefore bounds the
  * capacity a caller needs.
  * Tile ids are global over the cameras: camera c's tiles follow those of

@@ -206,8 +206,10 @@ def scene_grads(scene, cam, gC, gT, params=None, window=None):
     return g
 
 
-def dupsort_f32(foot, dkey, width, height, tile_w, tile_h, cap=None):
-    """Duplicate + stable sort of binary32 footprints: (keys, vals, ranges)."""
+def dupsort_f32(foot, dkey, width, height, tile_w, tile_h, cap=None, chol=None, rho2=None):
+    """Duplicate + stable sort of binary32 footprints: (keys, vals, ranges).
+    Without chol every support-box tile is listed; with chol [R][3] = l00 l01
+    l11 and rho2 [R] (binary32) only the tiles the support ellipse reaches."""
     R = foot.shape[0]
     foot = np.ascontiguousarray(foot, dtype=np.float32)
     dkey = np.ascontiguousarray(dkey, dtype=np.uint32)
@@ -218,7 +220,11 @@ def dupsort_f32(foot, dkey, width, height, tile_w, tile_h, cap=None):
         cap = min(int(R) * tiles, 50_000_000)
     keys = np.zeros(cap, dtype=np.uint32)
     vals = np.zeros(cap, dtype=np.uint32)
-    K = lib().lso_dupsort_f32(ctypes.c_longlong(R), _p(foot), _p(dkey), ctypes.c_int(width), ctypes.c_int(height),
+    if chol is not None:
+        chol = np.ascontiguousarray(chol, dtype=np.float32)
+        rho2 = np.ascontiguousarray(rho2, dtype=np.float32)
+    K = lib().lso_dupsort_f32(ctypes.c_longlong(R), _p(foot), _p(dkey), _p(chol) if chol is not None else None,
+                              _p(rho2) if chol is not None else None, ctypes.c_int(width), ctypes.c_int(height),
                               ctypes.c_int(tile_w), ctypes.c_int(tile_h), ctypes.c_longlong(cap), _p(keys), _p(vals),
                               _p(ranges))
     if K < 0:

@@ -505,22 +505,98 @@ int lso_rect(double mx, double my, double ex, double ey, int W, int H, int f32, 
   return r.empty ? 0 : 1;
 }
 
+// Tiles of support-box row ty that a record's support ellipse reaches, in
+// binary32 with every operation rounded once (the rule the tile lists
+// follow): the ellipse D^2 <= L, L = 1.02 rho^2 + 1e-3, D^2 = (l00 dx +
+// l01 dy)^2 + (l11 dy)^2, cut by the row's band of pixel-centre heights
+// (widened by 0.01 px), is convex; its x-extent follows from its left and
+// right boundaries at the leftmost / rightmost point's dy clamped into the
+// band (widened by 0.01 px), and a tile is reached when its pixel-centre
+// columns meet that extent.  Boxes of at most 2 tiles are taken whole.
+// Result [tx_a, tx_b] clamped to the box columns [x0, x1] (empty: tx_b < tx_a).
+struct ReachRec {
+  bool whole;
+  float mx, my, a01, inv_l00, l11, L, dyl, ext;
+};
+static ReachRec reach_rec(float mx, float my, float l00, float l01, float l11, float rho2, int box_tiles) {
+  ReachRec t{};
+  t.whole = box_tiles <= 2;
+  if (t.whole) return t;
+  volatile float L = std::fma(rho2, 1.02f, 1e-3f);
+  volatile float sL = std::sqrt((float)L);
+  volatile float inv_l00 = 1.f / l00;
+  volatile float a01 = l01 * inv_l00;
+  volatile float nn = std::fma(l11, l11, l01 * l01);
+  volatile float nrm = std::sqrt((float)nn);
+  volatile float num = sL * l01, den = l11 * nrm;
+  t.mx = mx;
+  t.my = my;
+  t.a01 = a01;
+  t.inv_l00 = inv_l00;
+  t.l11 = l11;
+  t.L = L;
+  t.dyl = num / den;
+  t.ext = sL / l11;
+  return t;
+}
+static void reach_row(const ReachRec& t, int ty, int TW, int TH, int x0, int x1, int& tx_a, int& tx_b) {
+  if (t.whole) {
+    tx_a = x0;
+    tx_b = x1;
+    return;
+  }
+  const float eps = 0.01f;
+  volatile float Y0 = (float)(ty * TH) + 0.5f;
+  volatile float Y1 = Y0 + (float)(TH - 1);
+  volatile float a = Y0 - t.my, b = Y1 - t.my;
+  volatile float lo0 = a - eps, hi0 = b + eps;
+  const float lo = std::fmax((float)lo0, -t.ext), hi = std::fmin((float)hi0, t.ext);
+  tx_a = x0;
+  tx_b = x0 - 1;
+  if (!(lo <= hi)) return;
+  const float d1 = std::fmin(std::fmax(t.dyl, lo), hi), d2 = std::fmin(std::fmax(-t.dyl, lo), hi);
+  volatile float e1 = t.l11 * d1, e2 = t.l11 * d2;
+  volatile float s1 = std::sqrt(std::fmax(std::fma(-(float)e1, (float)e1, t.L), 0.f));
+  volatile float s2 = std::sqrt(std::fmax(std::fma(-(float)e2, (float)e2, t.L), 0.f));
+  volatile float p1 = t.a01 * d1, p2 = t.a01 * d2;
+  volatile float f1 = std::fma((float)s1, t.inv_l00, (float)p1), f2 = std::fma((float)s2, t.inv_l00, -(float)p2);
+  volatile float xl0 = t.mx - f1, xh0 = t.mx + f2;
+  volatile float xlo = xl0 - eps, xhi = xh0 + eps;
+  const float inv_tw = 1.f / (float)TW;
+  volatile float xa = xlo + 0.5f, xb = xhi - 0.5f;
+  volatile float ga = std::fma((float)xa, inv_tw, -1.f), gb = xb * inv_tw;
+  const float fa = std::ceil((float)ga), fb = std::floor((float)gb);
+  tx_a = fa <= (float)x0 ? x0 : (fa > (float)x1 ? x1 + 1 : (int)fa);
+  tx_b = fb >= (float)x1 ? x1 : (fb < (float)x0 ? x0 - 1 : (int)fb);
+}
+
 // Duplication + stable sort of binary32 footprints (the integer part of the
 // pipeline).  foot [R][4] = mx my ex ey (float), dkey [R] = depth bits or
-// 0xFFFFFFFF when invisible.  Keys are tile ids (tile_base + ty*tiles_x + tx),
-// values record ids, ordered by (tile, dkey, id).  ranges [2*tiles] =
-// start/end per tile.  Returns K, or -1 when K exceeds cap.
-long long lso_dupsort_f32(long long R, const float* foot, const uint32_t* dkey, int W, int H, int TW, int TH,
-                          long long cap, uint32_t* keys, uint32_t* vals, int32_t* ranges) {
+// 0xFFFFFFFF when invisible.  Without ellipses (chol == NULL) every tile of
+// the support box gets a key; with chol [R][3] = l00 l01 l11 and rho2 [R]
+// (binary32, mx my from foot) only the tiles reach_row gives.  Keys are tile
+// ids (ty*tiles_x + tx), values record ids, ordered by (tile, dkey, id).
+// ranges [2*tiles] = start/end per tile.  Returns K, or -1 when K exceeds cap.
+long long lso_dupsort_f32(long long R, const float* foot, const uint32_t* dkey, const float* chol,
+                          const float* rho2, int W, int H, int TW, int TH, long long cap, uint32_t* keys,
+                          uint32_t* vals, int32_t* ranges) {
   int tx_n = (W + TW - 1) / TW, ty_n = (H + TH - 1) / TH;
   std::vector<std::pair<uint64_t, uint32_t>> kv;  // (tile << 32 | dkey, id), emitted in id order
   for (long long r = 0; r < R; ++r) {
     if (dkey[r] == 0xFFFFFFFFu) continue;
     Rect rc = rect_f32(foot[4 * r], foot[4 * r + 1], foot[4 * r + 2], foot[4 * r + 3], W, H);
     if (rc.empty) continue;
-    for (int ty = rc.y0 / TH; ty <= rc.y1 / TH; ++ty)
-      for (int tx = rc.x0 / TW; tx <= rc.x1 / TW; ++tx)
-        kv.push_back({((uint64_t)(ty * tx_n + tx) << 32) | dkey[r], (uint32_t)r});
+    const int x0 = rc.x0 / TW, x1 = rc.x1 / TW, y0 = rc.y0 / TH, y1 = rc.y1 / TH;
+    ReachRec t{};
+    t.whole = true;
+    if (chol)
+      t = reach_rec(foot[4 * r], foot[4 * r + 1], chol[3 * r], chol[3 * r + 1], chol[3 * r + 2], rho2[r],
+                    (x1 - x0 + 1) * (y1 - y0 + 1));
+    for (int ty = y0; ty <= y1; ++ty) {
+      int a, b;
+      reach_row(t, ty, TW, TH, x0, x1, a, b);
+      for (int tx = a; tx <= b; ++tx) kv.push_back({((uint64_t)(ty * tx_n + tx) << 32) | dkey[r], (uint32_t)r});
+    }
   }
   std::stable_sort(kv.begin(), kv.end(), [](const std::pair<uint64_t, uint32_t>& a,
                                             const std::pair<uint64_t, uint32_t>& b) { return a.first < b.first; });

@@ -144,7 +144,7 @@ DupWs dup_layout(char* base, int64_t R, int64_t cap, int key_passes) {
   w.v_alt = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.zero_begin = off;
   w.tmp_ctr = reinterpret_cast<unsigned long long*>(take(8));
-  w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4, SORT_ITEMS_SMALL));
+  w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4));
   w.tile_scratch = take(sort_scratch_bytes((int64_t)Cz, key_passes));
   w.zero_bytes = off - w.zero_begin;
   w.total = off;
@@ -225,7 +225,7 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
   LS_TRY(cudaMemsetAsync(static_cast<char*>(workspace) + w.zero_begin, 0, w.zero_bytes, st));
   // depth sort of the records: key = binary32 depth bits (0xFFFFFFFF when
   // culled), value = record id; four 8-bit passes, the last lands in (dk_a, dv_a)
-  SortScratch ds = sort_scratch_carve(w.depth_scratch, R > 0 ? R : 1, 4, SORT_ITEMS_SMALL);
+  SortScratch ds = sort_scratch_carve(w.depth_scratch, R > 0 ? R : 1, 4);
   if (R > 0) {
     LS_TRY(launch_radix_hist(pp.dkey, nullptr, R, 0, 4, ds.hist, st));
     LS_TRY(launch_radix_scan(ds.hist, 4, st));
@@ -266,15 +266,15 @@ ls_status ls_duplicate_sort(int64_t n_records, const void* proj, const ls_camera
     ea.dshift[p] = td.shift[p];
     ea.dmask[p] = (1u << td.bits[p]) - 1u;
   }
+  SortScratch ts = sort_scratch_carve(w.tile_scratch, key_capacity > 0 ? key_capacity : 1, kp);
+  ea.tile_hist = ts.hist;  // digits of the keys are counted where they are written
   LS_TRY(launch_enum_keys(false, ENUM_ALL, ea, st));
   LS_TRY(launch_dup_scan(enum_warps(R), w.warp_counts, key_capacity, n_keys_dev, w.n_valid, status_dev, st));
-  SortScratch ts = sort_scratch_carve(w.tile_scratch, key_capacity > 0 ? key_capacity : 1, kp);
   // ranges: accumulated by the last tile pass as (min start, ~max end)
   LS_TRY(cudaMemsetAsync(tile_ranges, 0xFF, sizeof(int32_t) * 2 * (size_t)total_tiles, st));
   if (R > 0 && key_capacity > 0) {
     ea.keys = ek;
     ea.vals = ev;
-    ea.tile_hist = ts.hist;
     LS_TRY(launch_enum_keys(true, ENUM_ALL, ea, st));
     LS_TRY(launch_radix_scan(ts.hist, kp, st));
     for (int p = 0; p < kp; ++p) {
@@ -573,7 +573,7 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
   w.n_held_valid = reinterpret_cast<int64_t*>(take(8));
   w.n_refuted = reinterpret_cast<unsigned*>(take(4));
   w.key_total = reinterpret_cast<unsigned long long*>(take(8));
-  w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4, SORT_ITEMS_SMALL));
+  w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4));
   w.kept_scratch = take(sort_scratch_bytes((int64_t)Cz, kp));
   w.held_scratch = take(sort_scratch_bytes((int64_t)Cz, kp));
   w.zero_bytes = off - w.zero_begin;
@@ -661,7 +661,7 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   // projection and depth order (as the plain path)
   if (R > 0) {
     LS_TRY(launch_project_fwd(n, means, scales, quats, opacities, sh, T, P, pw, nullptr, st));
-    SortScratch ds = sort_scratch_carve(w.depth_scratch, R, 4, SORT_ITEMS_SMALL);
+    SortScratch ds = sort_scratch_carve(w.depth_scratch, R, 4);
     LS_TRY(launch_radix_hist(pp.dkey, nullptr, R, 0, 4, ds.hist, st));
     LS_TRY(launch_radix_scan(ds.hist, 4, st));
     LS_TRY(launch_onesweep_pass(pp.dkey, nullptr, w.dk_b, w.dv_b, nullptr, R, R, 0, 8, 0, ds, nullptr, status_dev, st));
@@ -712,12 +712,12 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   ea.tmp_cap = key_capacity;
   ea.tmp_ctr = w.tmp_ctr_kept;
   ea.n_valid = w.n_kept_valid;
+  ea.tile_hist = ks.hist;
   LS_TRY(launch_enum_keys(false, ENUM_KEPT, ea, st));
   LS_TRY(launch_dup_scan(enum_warps(R), w.wc_kept, key_capacity, w.n_kept, w.n_kept_valid, status_dev, st));
   if (R > 0 && key_capacity > 0) {
     ea.keys = ek;
     ea.vals = ev;
-    ea.tile_hist = ks.hist;
     LS_TRY(launch_enum_keys(true, ENUM_KEPT, ea, st));
     ls_status s = tile_sort(ek, ev, ok, ov, w.n_kept_valid, key_capacity, kp, ks, w.k_ranges, tiles, status_dev, st);
     if (s != LS_OK) return s;
@@ -742,13 +742,12 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   ea.tmp_ctr = w.tmp_ctr_held;
   ea.n_valid = w.n_held_valid;
   ea.keys = ea.vals = nullptr;
-  ea.tile_hist = nullptr;
+  ea.tile_hist = hs.hist;
   LS_TRY(launch_enum_keys(false, ENUM_HELD, ea, st));
   LS_TRY(launch_dup_scan(enum_warps(R), w.wc_held, key_capacity, w.n_held, w.n_held_valid, status_dev, st));
   if (R > 0 && key_capacity > 0) {
     ea.keys = hk;
     ea.vals = hv;
-    ea.tile_hist = hs.hist;
     LS_TRY(launch_enum_keys(true, ENUM_HELD, ea, st));
     ls_status s = tile_sort(hk, hv, hok, hov, w.n_held_valid, key_capacity, kp, hs, w.h_ranges, tiles, status_dev, st);
     if (s != LS_OK) return s;

@@ -125,16 +125,13 @@ __global__ void __launch_bounds__(1024) dup_scan_kernel(int64_t n, uint32_t* cou
   }
 }
 
-// The condition of each mode on a reached candidate (key, record depth bits):
+// The condition of each mode on a key its record reaches (depth bits dk):
 // ENUM_ALL none; ENUM_KEPT depth bits <= the tile's proposal; ENUM_HELD the
 // tile is refuted and the depth is beyond its proposal.  In the count launch
 // of ENUM_KEPT a reached key beyond the proposal flags its tile in has_held.
 template <int MODE, bool COUNT>
-__device__ __forceinline__ bool cand_taken(const EnumArgs& A, const float4& g1, const float4& g2, uint32_t dk, int tx,
-                                           int ty, uint32_t key, uint32_t& reached) {
-  if (!tile_reached(g1, g2, tx, ty, A.tile_w, A.tile_h)) return false;
+__device__ __forceinline__ bool key_taken(const EnumArgs& A, uint32_t dk, uint32_t key) {
   if (MODE == ENUM_ALL) return true;
-  ++reached;
   const uint32_t lim = __ldg(A.dstar_bits + key);
   if (MODE == ENUM_KEPT) {
     const bool kept = dk <= lim;
@@ -148,21 +145,22 @@ constexpr uint32_t NO_STASH = 0xFFFFFFFFu;
 
 // Keys of ENUM_WARP_RECS depth-ordered records per warp (emit.cuh).
 //
-// Count launch (EMIT = false): each warp walks its candidates, counts the
-// taken keys (warp_counts) and, when its whole box-candidate count fits in
-// the stash (tmp_*, bump-allocated per warp), also writes them there,
-// compacted (warp_tbase; NO_STASH otherwise).  ENUM_KEPT also adds every
-// reached key to *key_total and flags tiles in has_held.
-// Emit launch (EMIT = true), after the counts are scanned into offsets: a
-// stashed warp copies its keys to its offset; any other warp walks its
-// candidates again and writes them.  Both gather the tile-sort digit
-// histograms.  ENUM_HELD drops up front every record whose box holds no
-// refuted tile (summed-area table `sat`).
+// Count launch (EMIT = false): each warp walks its records' rows and keys,
+// counts the taken keys (warp_counts) and, when the whole box-tile count of
+// its records fits in the stash (tmp_*, bump-allocated per warp), also
+// writes them there, compacted (warp_tbase; NO_STASH otherwise), with their
+// tile-sort digits.  ENUM_KEPT also adds every reached key to *key_total and
+// flags tiles in has_held.  Emit launch (EMIT = true), after the counts are
+// scanned into offsets: a stashed warp copies its keys to its offset; any
+// other warp walks again and writes them (and their digits).  ENUM_HELD
+// drops up front every record whose box holds no refuted tile (summed-area
+// table `sat`).
 template <bool EMIT, int MODE>
 __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
   __shared__ EnumRec S[ENUM_WARPS][ENUM_WARP_RECS];
+  __shared__ uint4 SR[ENUM_WARPS][32];  // a step's rows with keys: {first key, first index, record, depth bits}
   __shared__ CamLite s_cam[LS_MAX_CAMS];
-  __shared__ uint32_t s_hist[EMIT ? 3 : 1][RADIX];
+  __shared__ uint32_t s_hist[3][RADIX];
   const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -176,15 +174,15 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
   }
   for (int c = tid; c < A.cams.n; c += ENUM_THREADS)
     s_cam[c] = CamLite{A.cams.c[c].W, A.cams.c[c].H, A.cams.c[c].tiles_x, A.cams.c[c].tile_base};
-  if (EMIT)
-    for (int i = tid; i < 3 * RADIX; i += ENUM_THREADS) (&s_hist[0][0])[i] = 0;
+  const bool hist = A.tile_hist != nullptr;
+  for (int i = tid; i < 3 * RADIX; i += ENUM_THREADS) (&s_hist[0][0])[i] = 0;
   __syncthreads();
   uint64_t out = 0;
   bool walk = true;
   if (EMIT) {
     out = A.out_base + (uint64_t)A.warp_counts[gw];
     const uint32_t tb = A.warp_tbase[gw];
-    if (tb != NO_STASH) {  // copy the stashed keys
+    if (tb != NO_STASH) {  // copy the stashed keys (their digits were counted then)
       walk = false;
       const uint64_t end = gw + 1 < A.n_warps ? A.out_base + (uint64_t)A.warp_counts[gw + 1]
                                               : A.out_base + (uint64_t)*A.n_valid;
@@ -206,17 +204,17 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
           if (i < n) {
             A.keys[out + i] = k[u];
             A.vals[out + i] = v[u];
-            for (int p = 0; p < A.key_passes; ++p) atomicAdd(&s_hist[p][(k[u] >> A.dshift[p]) & A.dmask[p]], 1u);
           }
         }
       }
     }
   }
   if (walk) {
-    // the warp's records with candidates, compacted, with their offsets
+    // the warp's records with a non-empty box, compacted, with the offsets of their rows
     EnumRec* W = S[warp];
+    uint4* SRw = SR[warp];
     int n_nz = 0;
-    uint32_t total = 0;
+    uint32_t total = 0, box_total = 0;
     const int sx = s_cam[0].tiles_x + 1;
 #pragma unroll
     for (int i = 0; i < ENUM_WARP_RECS / 32; ++i) {
@@ -228,39 +226,42 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
         r = A.order[j];
         if (MODE != ENUM_ALL) dk = A.dkey_sorted[j];
       }
-      uint32_t cnt = box_count(rc);
-      if (MODE == ENUM_HELD && cnt) {
+      if (MODE == ENUM_HELD && box_rows(rc)) {
         const int x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF, y1 = rc.y >> 16;
         const int* sat = A.sat;
         if (sat[(y1 + 1) * sx + x1 + 1] - sat[y0 * sx + x1 + 1] - sat[(y1 + 1) * sx + x0] + sat[y0 * sx + x0] == 0)
-          cnt = 0u;
+          rc = make_uint2(1u, 0u);
       }
-      uint32_t x = cnt;
+      const uint32_t rows = box_rows(rc);
+      uint32_t x = rows, bx = box_count(rc);
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t u = __shfl_up_sync(FULL, x, o);
         if (lane >= o) x += u;
+        bx += __shfl_xor_sync(FULL, bx, o);
       }
-      const unsigned nz = __ballot_sync(FULL, cnt > 0);
-      if (cnt) {
+      const unsigned nz = __ballot_sync(FULL, rows > 0);
+      if (rows) {
         const CamLite cm = s_cam[A.cams.n > 1 ? r / (uint32_t)A.n_per_cam : 0u];
-        enum_rec(W[n_nz + __popc(nz & lt)], total + x - cnt, rc, r, dk, cm, A.rec);
+        enum_rec(W[n_nz + __popc(nz & lt)], total + x - rows, rc, r, dk, cm, A.rec);
       }
       n_nz += __popc(nz);
       total += __shfl_sync(FULL, x, 31);
+      box_total += bx;
     }
     __syncwarp();
-    // count launch: a stash region for every box candidate of the warp
+    // count launch: a stash region for every box tile of the warp's records
     uint32_t tb = NO_STASH;
     if (!EMIT) {
-      if (lane == 0 && total > 0) {
-        const unsigned long long b = atomicAdd(A.tmp_ctr, (unsigned long long)total);
-        if (b + total <= (unsigned long long)A.tmp_cap) tb = (uint32_t)b;
+      if (lane == 0 && box_total > 0) {
+        const unsigned long long b = atomicAdd(A.tmp_ctr, (unsigned long long)box_total);
+        if (b + box_total <= (unsigned long long)A.tmp_cap) tb = (uint32_t)b;
       }
       tb = __shfl_sync(FULL, tb, 0);
     }
+    const bool store = EMIT || tb != NO_STASH;
     uint32_t kept = 0, reached = 0;
-    int sp = 0;  // record of the step's first candidate
+    int sp = 0;  // record of the step's first row
     for (uint32_t cb = 0; cb < total; cb += 32) {
       // lane i marks where record sp + 1 + i starts, when inside this step;
       // lane l's record is sp plus the number of marks at or below l
@@ -270,34 +271,85 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
         const uint32_t d = W[ns].off - cb;
         if (d < 32u) mark = 1u << d;
       }
-      const uint32_t M = __reduce_or_sync(FULL, mark);
-      const int sl = sp + __popc(M & ((2u << lane) - 1u));
+      const int sl = sp + __popc(__reduce_or_sync(FULL, mark) & ((2u << lane) - 1u));
       const uint32_t e = cb + lane;
-      bool take = false;
-      uint32_t key = 0, r = 0;
+      uint32_t n = 0, key0 = 0, r = 0, dk = 0;
       if (e < total) {
         const uint4* q = reinterpret_cast<const uint4*>(&W[sl]);
         const uint4 g0 = q[0], g3 = q[3];
         const float4 g1 = reinterpret_cast<const float4*>(q)[1], g2 = reinterpret_cast<const float4*>(q)[2];
-        int tx, ty;
-        key = cand_key(g0, __uint_as_float(g3.z), e - g0.x, tx, ty);
-        take = cand_taken<MODE, !EMIT>(A, g1, g2, g3.y, tx, ty, key, reached);
+        const int row = (int)(e - g0.x), x0 = (int)(g0.w & 0xFFFFu), y0 = (int)(g0.w >> 16);
+        int tx_a, tx_b;
+        row_range(g1, g2, y0 + row, A.tile_w, A.tile_h, x0, x0 + (int)(g0.z & 0xFFFFu) - 1, tx_a, tx_b);
+        if (tx_b >= tx_a) {
+          n = (uint32_t)(tx_b - tx_a + 1);
+          key0 = g0.y + (uint32_t)row * (g0.z >> 16) + (uint32_t)(tx_a - x0);
+        }
         r = g3.x;
+        dk = g3.y;
       }
       sp = __shfl_sync(FULL, sl, 31);
-      const unsigned bal = __ballot_sync(FULL, take);
-      if (take) {
-        const uint32_t rank = kept + __popc(bal & lt);
-        if (EMIT) {
-          A.keys[out + rank] = key;
-          A.vals[out + rank] = r;
-          for (int p = 0; p < A.key_passes; ++p) atomicAdd(&s_hist[p][(key >> A.dshift[p]) & A.dmask[p]], 1u);
-        } else if (tb != NO_STASH) {
-          A.tmp_keys[tb + rank] = key;
-          A.tmp_vals[tb + rank] = r;
-        }
+      // this step's rows with keys, compacted, and the walk over their keys
+      uint32_t xs = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(FULL, xs, o);
+        if (lane >= o) xs += u;
       }
-      kept += __popc(bal);
+      const unsigned rz = __ballot_sync(FULL, n > 0);
+      if (n) SRw[__popc(rz & lt)] = make_uint4(key0, xs - n, r, dk);
+      const uint32_t keys_here = __shfl_sync(FULL, xs, 31);
+      const int n_rows = __popc(rz);
+      reached += n;
+      __syncwarp();
+      int sq = 0;
+      for (uint32_t c2 = 0; c2 < keys_here; c2 += 32) {
+        const int ms = sq + 1 + lane;
+        uint32_t mk = 0;
+        if (ms < n_rows) {
+          const uint32_t d = SRw[ms].y - c2;
+          if (d < 32u) mk = 1u << d;
+        }
+        const int sj = sq + __popc(__reduce_or_sync(FULL, mk) & ((2u << lane) - 1u));
+        const uint32_t e2 = c2 + lane;
+        bool take = false;
+        uint32_t key = 0, rr = 0;
+        if (e2 < keys_here) {
+          const uint4 rw = SRw[sj];
+          key = rw.x + (e2 - rw.y);
+          rr = rw.z;
+          take = key_taken<MODE, !EMIT>(A, rw.w, key);
+        }
+        sq = __shfl_sync(FULL, sj, 31);
+        const unsigned bal = __ballot_sync(FULL, take);
+        if (take && store) {
+          const uint32_t rank = kept + __popc(bal & lt);
+          if (EMIT) {
+            A.keys[out + rank] = key;
+            A.vals[out + rank] = rr;
+          } else {
+            A.tmp_keys[tb + rank] = key;
+            A.tmp_vals[tb + rank] = rr;
+          }
+        }
+        if (hist && store && bal) {
+          // low digit: consecutive tiles, distinct per lane; higher digits:
+          // usually one value for the whole step, added once
+          if (take) atomicAdd(&s_hist[0][(key >> A.dshift[0]) & A.dmask[0]], 1u);
+          const int first = __ffs(bal) - 1;
+          for (int p = 1; p < A.key_passes; ++p) {
+            const uint32_t d = (key >> A.dshift[p]) & A.dmask[p];
+            const uint32_t d0 = __shfl_sync(FULL, d, first);
+            if (__all_sync(FULL, !take || d == d0)) {
+              if (lane == first) atomicAdd(&s_hist[p][d0], (uint32_t)__popc(bal));
+            } else if (take) {
+              atomicAdd(&s_hist[p][d], 1u);
+            }
+          }
+        }
+        kept += __popc(bal);
+      }
+      __syncwarp();  // the rows of this step are read before the next step rewrites them
     }
     if (!EMIT) {
       if (MODE == ENUM_KEPT) {
@@ -311,7 +363,7 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
       }
     }
   }
-  if (!EMIT) return;
+  if (!hist) return;
   __syncthreads();
   for (int i = tid; i < A.key_passes * RADIX; i += ENUM_THREADS) {
     const uint32_t v = (&s_hist[0][0])[i];

@@ -1,22 +1,20 @@
 // Enumeration of (record, tile) keys, shared by the plain duplication and the
 // learned path's kept / held-out enumerations (duplicate.cu).
 //
-// A warp takes ENUM_WARP_RECS consecutive records of the depth order.  Their
-// candidates are the tiles of their binary32 support boxes; a candidate is
-// taken when the support ellipse reaches the tile (tile_reached) and the
-// mode's condition holds.  The warp first keeps only the records with
-// candidates (ballot compaction into shared memory, with the per-record
-// constants of the reach test) and scans their candidate counts.  Then it
-// walks the candidates 32 at a time: lane l takes candidate e = step + l;
-// the lanes holding the next records' first candidates mark them in one
-// warp OR-reduction, so lane l's record is the step's first record plus the
-// number of marks at or below l (no search), and its tile follows from one
-// division done in binary32 and corrected to the exact quotient.  Taken
-// candidates are compacted with a ballot.  A count launch records each
-// warp's total; after a scan of the totals, the emit launch walks the same
-// candidates in the same order and writes the taken keys from the warp's
-// offset, so keys come out in depth order and every tile's keys in
-// (depth, id) order.
+// A warp takes ENUM_WARP_RECS consecutive records of the depth order and
+// keeps those with a non-empty support box (ballot compaction into shared
+// memory, with the constants of their row ranges).  It then walks their box
+// rows 32 at a time: lane l takes row e = step + l; the lanes holding the
+// next records' first rows mark them in one warp OR-reduction, so lane l's
+// record is the step's first record plus the number of marks at or below l
+// (no search).  Each row gives, in closed form, the contiguous run of tiles
+// the support ellipse reaches in it (row_range); the rows with tiles are
+// compacted and their keys walked 32 at a time with the same marking, the
+// mode's condition applied per key, and the taken keys compacted with a
+// ballot.  A count launch records each warp's total (and stashes its keys
+// in a spare buffer); after a scan of the totals, the emit launch copies or
+// writes them from the warp's offset, so keys come out in depth order and
+// every tile's keys in (depth, id) order.
 #pragma once
 
 #include "kernels.h"
@@ -32,89 +30,102 @@ struct CamLite {
   int W, H, tiles_x, tile_base;
 };
 
-// One compacted record of a warp: its candidates and the reach-test
-// constants, as four 16-byte words (one shared load each).
+// One compacted record of a warp, as four 16-byte words (one shared load
+// each): where its box rows start in the warp's row list, its box, and the
+// constants of its row ranges.
 struct __align__(16) EnumRec {
-  uint32_t off;          // warp-exclusive offset of its first candidate
+  uint32_t off;          // warp-exclusive offset of its first box row
   uint32_t kb;           // key of its first box tile
   uint32_t wt;           // box width in tiles | camera tiles_x << 16
   uint32_t xy;           // first tile column | first tile row << 16
-  float mx, my, l00, l01;
-  float l11;
+  float mx, my;          // centre
+  float a01;             // l01 / l00
   float inv_l00;         // 1 / l00
-  float kq;              // l00 l01 / (l01^2 + l11^2)
-  float lim;             // accepted bound on D^2
+  float l11;
+  float lim;             // accepted bound L on D^2
+  float dyl;             // dy of the leftmost point of D^2 = L
+  float ext_y;           // half height of D^2 = L: sqrt(L) / l11
   uint32_t r, dk;        // record id, depth bits
-  float rw;              // 1 / box width
-  uint32_t pad;
+  uint32_t pad0, pad1;
 };
 
 __device__ __forceinline__ uint32_t box_count(uint2 rc) {
   const int x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF, y1 = rc.y >> 16;
   return x1 < x0 ? 0u : (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
 }
+__device__ __forceinline__ uint32_t box_rows(uint2 rc) {
+  const int x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF, y1 = rc.y >> 16;
+  return x1 < x0 ? 0u : (uint32_t)(y1 - y0 + 1);
+}
 
+// The support ellipse, loosened so that binary32 rounding of D^2 in the
+// blend can never composite a pair in a tile left out: D^2 <= L with
+// L = 1.02 rho^2 + 1e-3 (D^2 = |L d|^2 for the upper Cholesky factor
+// [[l00, l01], [0, l11]] of the conic), and every range below widened by
+// RANGE_EPS pixels.
+constexpr float RANGE_EPS = 0.01f;
+
+// Boxes of at most WHOLE_BOX tiles are listed whole: the ellipse reaches
+// nearly all of their tiles, and their records skip the gather of the
+// ellipse.
+constexpr uint32_t WHOLE_BOX = 2;
+
+// Every operation below is rounded explicitly (no contraction), so the
+// lists can be reproduced bit for bit in binary32 elsewhere.
 __device__ __forceinline__ void enum_rec(EnumRec& t, uint32_t off, uint2 rc, uint32_t r, uint32_t dk,
                                          const CamLite& cm, const float4* __restrict__ rec) {
   const uint32_t x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF;
   const uint32_t w = x1 - x0 + 1;
-  const float4 a = rec[3 * (size_t)r], b = rec[3 * (size_t)r + 1];  // {mx, my, l00, l01}, {l11, o, rho2, depth}
   uint4* q = reinterpret_cast<uint4*>(&t);
   q[0] = make_uint4(off, (uint32_t)cm.tile_base + y0 * (uint32_t)cm.tiles_x + x0, w | ((uint32_t)cm.tiles_x << 16),
                     x0 | (y0 << 16));
-  reinterpret_cast<float4*>(&t)[1] = a;
-  reinterpret_cast<float4*>(&t)[2] =
-      make_float4(b.x, 1.f / a.z, a.z * a.w / fmaf(a.w, a.w, b.x * b.x), fmaf(b.z, 1.02f, 1e-3f));
-  q[3] = make_uint4(r, dk, __float_as_uint(1.f / (float)w), 0u);
-}
-
-// The reach test of one candidate: a record's geometry words g1 = {mx, my,
-// l00, l01} and g2 = {l11, 1/l00, l00 l01 / (l01^2 + l11^2), bound}.
-//
-// Whether the support ellipse q(p - mu) <= rho^2, q = |L d|^2 for the upper
-// Cholesky factor L = [[l00, l01], [0, l11]] of the conic, reaches the
-// rectangle spanned by the pixel centres of tile (tx, ty).  A convex q whose
-// minimum lies outside the rectangle attains its minimum over it on a side
-// that faces the centre; the minimum along the facing row and along the
-// facing column are both taken (each by clamping the 1D minimiser; a side
-// that does not face the centre still gives a point of the rectangle, so the
-// smaller value is the minimum), and the centre itself when inside.  The
-// bound is loosened by 2 % (+1e-3) so that binary32 rounding of q in the
-// blend can never composite a pair in a tile this test left out.
-__device__ __forceinline__ bool tile_reached(const float4& g1, const float4& g2, int tx, int ty, int TW, int TH) {
-  const float mx = g1.x, my = g1.y, l00 = g1.z, l01 = g1.w, l11 = g2.x;
-  const float X0 = (float)(tx * TW) + 0.5f, X1 = X0 + (float)(TW - 1);
-  const float Y0 = (float)(ty * TH) + 0.5f, Y1 = Y0 + (float)(TH - 1);
-  const bool inside = mx >= X0 && mx <= X1 && my >= Y0 && my <= Y1;
-  // facing row: dx* = -l01 dy / l00
-  const float dyr = (my < Y0 ? Y0 : Y1) - my;
-  const float dxr = fminf(fmaxf(-l01 * dyr * g2.y, X0 - mx), X1 - mx);
-  const float e1r = fmaf(l00, dxr, l01 * dyr), e2r = l11 * dyr;
-  // facing column: dy* = -l00 l01 dx / (l01^2 + l11^2)
-  const float dxc = (mx < X0 ? X0 : X1) - mx;
-  const float dyc = fminf(fmaxf(-g2.z * dxc, Y0 - my), Y1 - my);
-  const float e1c = fmaf(l00, dxc, l01 * dyc), e2c = l11 * dyc;
-  const float best = fminf(fmaf(e1r, e1r, e2r * e2r), fmaf(e1c, e1c, e2c * e2c));
-  return inside || best <= g2.w;
-}
-
-// Candidate m (row-major in the box) of a record with words g0 = {off, kb,
-// wt, xy} and 1 / width rw: its key and tile.  m < 2^24, so float(m) is exact
-// and the binary32 quotient is within one of m / w.
-__device__ __forceinline__ uint32_t cand_key(const uint4& g0, float rw, uint32_t m, int& tx, int& ty) {
-  const int w = (int)(g0.z & 0xFFFFu);
-  int q = (int)__float2uint_rz(__uint2float_rn(m) * rw);
-  int rem = (int)m - q * w;
-  if (rem < 0) {
-    --q;
-    rem += w;
-  } else if (rem >= w) {
-    ++q;
-    rem -= w;
+  q[3] = make_uint4(r, dk, 0u, 0u);
+  if (box_count(rc) <= WHOLE_BOX) {
+    reinterpret_cast<float4*>(&t)[2] = make_float4(0.f, 0.f, 0.f, -1.f);  // ext_y < 0: the whole box
+    return;
   }
-  tx = (int)(g0.w & 0xFFFFu) + rem;
-  ty = (int)(g0.w >> 16) + q;
-  return g0.y + (uint32_t)q * (g0.z >> 16) + (uint32_t)rem;
+  const float4 a = rec[3 * (size_t)r], b = rec[3 * (size_t)r + 1];  // {mx, my, l00, l01}, {l11, o, rho2, depth}
+  const float L = __fmaf_rn(b.z, 1.02f, 1e-3f), sL = __fsqrt_rn(L);
+  const float inv_l00 = __fdiv_rn(1.f, a.z);
+  reinterpret_cast<float4*>(&t)[1] = make_float4(a.x, a.y, __fmul_rn(a.w, inv_l00), inv_l00);
+  // leftmost point of the ellipse: dy = sqrt(L) l01 / (l11 sqrt(l11^2 + l01^2))
+  const float nrm = __fsqrt_rn(__fmaf_rn(b.x, b.x, __fmul_rn(a.w, a.w)));
+  reinterpret_cast<float4*>(&t)[2] =
+      make_float4(b.x, L, __fdiv_rn(__fmul_rn(sL, a.w), __fmul_rn(b.x, nrm)), __fdiv_rn(sL, b.x));
+}
+
+// The tiles of box row ty that the ellipse reaches: [tx_a, tx_b] (empty when
+// tx_b < tx_a), clamped to the box columns [x0, x1].  The ellipse cut by the
+// row's band of pixel-centre heights [Y0, Y1] is convex, so the tiles it
+// reaches are those whose pixel-centre columns meet its x-extent
+// [X_lo, X_hi]; X_lo is the convex left boundary
+// x(dy) = mx - (sqrt(L - (l11 dy)^2) + l01 dy) / l00 minimised over the band
+// (at the leftmost point's dy, clamped into the band), X_hi the mirror.
+__device__ __forceinline__ void row_range(const float4& g1, const float4& g2, int ty, int TW, int TH, int x0, int x1,
+                                          int& tx_a, int& tx_b) {
+  const float mx = g1.x, my = g1.y, a01 = g1.z, inv_l00 = g1.w, l11 = g2.x, L = g2.y, dyl = g2.z, ext = g2.w;
+  if (ext < 0.f) {  // a small box, listed whole
+    tx_a = x0;
+    tx_b = x1;
+    return;
+  }
+  const float Y0 = __fadd_rn((float)(ty * TH), 0.5f), Y1 = __fadd_rn(Y0, (float)(TH - 1));
+  const float lo = fmaxf(__fsub_rn(__fsub_rn(Y0, my), RANGE_EPS), -ext);
+  const float hi = fminf(__fadd_rn(__fsub_rn(Y1, my), RANGE_EPS), ext);
+  tx_a = x0;
+  tx_b = x0 - 1;
+  if (!(lo <= hi)) return;
+  const float d1 = fminf(fmaxf(dyl, lo), hi), d2 = fminf(fmaxf(-dyl, lo), hi);
+  const float e1 = __fmul_rn(l11, d1), e2 = __fmul_rn(l11, d2);
+  const float s1 = __fsqrt_rn(fmaxf(__fmaf_rn(-e1, e1, L), 0.f)), s2 = __fsqrt_rn(fmaxf(__fmaf_rn(-e2, e2, L), 0.f));
+  const float xlo = __fsub_rn(__fsub_rn(mx, __fmaf_rn(s1, inv_l00, __fmul_rn(a01, d1))), RANGE_EPS);
+  const float xhi = __fadd_rn(__fadd_rn(mx, __fmaf_rn(s2, inv_l00, -__fmul_rn(a01, d2))), RANGE_EPS);
+  // tile tx holds pixel-centre columns [tx TW + 0.5, tx TW + TW - 0.5]
+  const float inv_tw = 1.f / (float)TW;  // exact: TW is a power of two
+  const float fa = ceilf(__fmaf_rn(__fadd_rn(xlo, 0.5f), inv_tw, -1.f));
+  const float fb = floorf(__fmul_rn(__fsub_rn(xhi, 0.5f), inv_tw));
+  tx_a = fa <= (float)x0 ? x0 : (fa > (float)x1 ? x1 + 1 : (int)fa);
+  tx_b = fb >= (float)x1 ? x1 : (fb < (float)x0 ? x0 - 1 : (int)fb);
 }
 
 }  // namespace ls

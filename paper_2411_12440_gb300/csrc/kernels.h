@@ -19,12 +19,10 @@ cudaError_t launch_project_bwd(int n, const float* means, const float* scales, c
 
 // ---- onesweep radix sort (sort.cu)
 constexpr int SORT_THREADS = 256;
-// Keys per thread of a partition: the key sorts run 15 (3840-key
-// partitions); the record-depth sort, a few million keys, runs 8 so that its
-// partitions fill the GPU in more than one wave.
+// Keys per thread of a partition (3840-key partitions; 8, 11, 19 and 24
+// measured slower on the bench frame, for the depth sort as well).
 constexpr int SORT_ITEMS = 15;
-constexpr int SORT_ITEMS_SMALL = 8;
-constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per partition (largest)
+constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per partition
 constexpr int RADIX = 256;
 
 // Scratch of one sort of up to `cap` keys over `passes` 8-bit digits.

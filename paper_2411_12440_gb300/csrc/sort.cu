@@ -307,7 +307,6 @@ cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_i
 #define LS_OS(B, I)                                                                                        \
   onesweep_launch<B, I>(keys_in, vals_in, keys_out, vals_out, n_dev, n_host, cap, shift, pass, s, ranges, status, \
                         st)
-  if (s.items == SORT_ITEMS_SMALL) return LS_OS(8, SORT_ITEMS_SMALL);  // depth sort: full bytes
   switch (bits) {
     case 4: return LS_OS(4, SORT_ITEMS);
     case 5: return LS_OS(5, SORT_ITEMS);

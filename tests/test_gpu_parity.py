@@ -31,13 +31,12 @@ def _dupsort(rz, proj, R, cams, cap):
 
 
 # ------------------------------------------------------------------ a2 + a3
-# The tile lists hold a (tile, record) pair when the record's support ellipse
-# reaches the tile (a conservative binary32 test), so they lie between two
-# oracle sets: every tile of the binary32 support box whose pixel centres the
-# ellipse (shrunk by 1e-3) contains must be listed, and nothing outside the
-# box may be.  What is unique is checked exactly: the listed pairs are the
-# oracle's box list filtered, in the oracle's (tile, depth, record id) order,
-# and the ranges delimit each tile's run.
+# A record is listed in the tiles of its binary32 support box that its
+# support ellipse reaches (a binary32 rule both sides compute with the same
+# roundings), so lists, orders and ranges are compared bit for bit with the
+# oracle.  Two more checks tie the rule to the method: the lists hold every
+# tile the oracle finds, by brute force over pixel centres, to be reached by
+# the (slightly shrunk) ellipse, and they are the support-box lists filtered.
 def _touch(rec, dkey, W, H, tw, th, shrink=0.999):
     foot = np.concatenate([rec["mean2d"], rec["ext"]], 1)
     l00, l01, l11 = (rec["chol"][:, k].astype(np.float64) for k in range(3))
@@ -45,41 +44,43 @@ def _touch(rec, dkey, W, H, tw, th, shrink=0.999):
     return oracle.touch_pairs(foot, dkey, conic, rec["rho2"].astype(np.float64), W, H, tw, th, shrink)
 
 
-def _check_lists(keys, vals, ranges, ok, ov, et, er):
-    """GPU (keys, vals, ranges) against the oracle's box lists (ok, ov) and the
-    pairs (et, er) that must be present."""
+def _oracle_lists(rec, dkey, W, H, tw, th, reach=True):
+    foot = np.concatenate([rec["mean2d"], rec["ext"]], 1)
+    if not reach:
+        return oracle.dupsort_f32(foot, dkey, W, H, tw, th)
+    return oracle.dupsort_f32(foot, dkey, W, H, tw, th, chol=rec["chol"], rho2=rec["rho2"])
+
+
+def _check_reach(keys, vals, ok, ov, et, er):
+    """GPU lists against the box lists (ok, ov) and the pairs (et, er) that
+    must be present; returns the fraction of box pairs listed."""
     R1 = np.int64(max(int(ov.max()) if len(ov) else 0, int(vals.max()) if len(vals) else 0) + 1)
     gid = keys.astype(np.int64) * R1 + vals.astype(np.int64)
     bid = ok.astype(np.int64) * R1 + ov.astype(np.int64)
     mask = np.isin(bid, gid)
     assert np.array_equal(bid[mask], gid), "listed pairs are not the box lists filtered, in order"
     assert np.isin(et.astype(np.int64) * R1 + er.astype(np.int64), gid).all(), "a reached tile is missing"
-    K = len(keys)
-    exp = np.zeros_like(ranges)
-    if K:
-        starts = np.r_[0, np.nonzero(np.diff(keys.astype(np.int64)))[0] + 1]
-        ends = np.r_[starts[1:], K]
-        exp[keys[starts], 0] = starts
-        exp[keys[starts], 1] = ends
-    assert np.array_equal(ranges, exp)
     return mask.mean() if len(mask) else 1.0
 
 
 @pytest.mark.parametrize("tile", TILES)
 @pytest.mark.parametrize("R,W,H", [(1, 300, 200), (3001, 300, 200), (40_000, 1297, 840)])
-def test_duplicate_sort_lists(tile, R, W, H):
+def test_duplicate_sort_bitexact(tile, R, W, H):
     rec = scenes.random_records(R, W, H, seed=R + tile[0])
     proj, dkey = pack_records(rec)
     P = raster.RenderParams(tile_w=tile[0], tile_h=tile[1])
     rz = raster.Rasterizer(P)
     cam = scenes.identity_camera(W, H)
-    foot = np.concatenate([rec["mean2d"], rec["ext"]], 1)
-    ok, ov, orr = oracle.dupsort_f32(foot, dkey, W, H, tile[0], tile[1])
+    ok, ov, orr = _oracle_lists(rec, dkey, W, H, tile[0], tile[1])
+    bk, bv, _ = _oracle_lists(rec, dkey, W, H, tile[0], tile[1], reach=False)
     et, er = _touch(rec, dkey, W, H, tile[0], tile[1])
-    keys, vals, ranges, K = _dupsort(rz, proj, R, [cam], cap=len(ok) + 17)
+    keys, vals, ranges, K = _dupsort(rz, proj, R, [cam], cap=len(bk) + 17)
     rz.check_status()
-    assert len(et) <= K <= len(ok)
-    frac = _check_lists(keys, vals, ranges, ok, ov, et, er)
+    assert K == len(ok)
+    assert np.array_equal(keys, ok)
+    assert np.array_equal(vals, ov)
+    assert np.array_equal(ranges, orr)
+    frac = _check_reach(keys, vals, bk, bv, et, er)
     if R > 1000:
         assert frac < 0.95  # the box corners the ellipses miss are dropped
 
@@ -91,12 +92,10 @@ def test_duplicate_sort_ties_and_culled():
     rec["depth"][:] = rec["depth"][:7].repeat(20_000 // 7 + 1)[:20_000]
     proj, dkey = pack_records(rec)
     rz = raster.Rasterizer(raster.RenderParams())
-    foot = np.concatenate([rec["mean2d"], rec["ext"]], 1)
-    ok, ov, orr = oracle.dupsort_f32(foot, dkey, W, H, 16, 16)
-    et, er = _touch(rec, dkey, W, H, 16, 16)
+    ok, ov, orr = _oracle_lists(rec, dkey, W, H, 16, 16)
     keys, vals, ranges, K = _dupsort(rz, proj, 20_000, [scenes.identity_camera(W, H)], cap=len(ok))
     rz.check_status()
-    _check_lists(keys, vals, ranges, ok, ov, et, er)
+    assert K == len(ok) and np.array_equal(keys, ok) and np.array_equal(vals, ov) and np.array_equal(ranges, orr)
 
 
 def test_duplicate_sort_empty_and_all_culled():
@@ -117,21 +116,17 @@ def test_duplicate_sort_capacity_overflow_reports_and_recovers():
     proj, dkey = pack_records(rec)
     rz = raster.Rasterizer(raster.RenderParams())
     cam = scenes.identity_camera(W, H)
-    foot = np.concatenate([rec["mean2d"], rec["ext"]], 1)
-    ok, ov, orr = oracle.dupsort_f32(foot, dkey, W, H, 16, 16)
-    et, er = _touch(rec, dkey, W, H, 16, 16)
-    _, _, _, K0 = _dupsort(rz, proj, 2000, [cam], cap=len(ok))
-    rz.check_status()
-    _, _, ranges, K = _dupsort(rz, proj, 2000, [cam], cap=K0 - 1)
-    assert K == K0  # the true count is reported
+    ok, ov, orr = _oracle_lists(rec, dkey, W, H, 16, 16)
+    _, _, ranges, K = _dupsort(rz, proj, 2000, [cam], cap=len(ok) - 1)
+    assert K == len(ok)  # the true count is reported
     assert not ranges.any()
     assert int(rz.status.item()) == 3
     with pytest.raises(N.LsError):
         rz.check_status()
     rz.reset_status()
-    keys, vals, ranges, K = _dupsort(rz, proj, 2000, [cam], cap=K0)
+    keys, vals, ranges, K = _dupsort(rz, proj, 2000, [cam], cap=len(ok))
     rz.check_status()
-    _check_lists(keys, vals, ranges, ok, ov, et, er)
+    assert np.array_equal(keys, ok) and np.array_equal(vals, ov) and np.array_equal(ranges, orr)
 
 
 def test_duplicate_sort_multi_camera_global_tiles():
@@ -145,21 +140,26 @@ def test_duplicate_sort_multi_camera_global_tiles():
     proj, dkey = pack_records(allrec)
     rz = raster.Rasterizer(raster.RenderParams())
     base = 0
-    exp_k, exp_v, exp_t, exp_rr = [], [], [], []
+    exp_k, exp_v, exp_r = [], [], []
     # oracle per camera, then merge: global order is (global tile, depth, record id)
     for i, (w, h) in enumerate(sizes):
-        foot = np.concatenate([recs[i]["mean2d"], recs[i]["ext"]], 1)
-        k, v, r = oracle.dupsort_f32(foot, dkey[i * n:(i + 1) * n], w, h, 16, 16)
+        k, v, r = _oracle_lists(recs[i], dkey[i * n:(i + 1) * n], w, h, 16, 16)
         exp_k.append(k + base)
         exp_v.append(v + i * n)
+        exp_r.append(r)
         base += raster.tiles_of(cams[i], rz.params)
-        t, rr_ = _touch(recs[i], dkey[i * n:(i + 1) * n], w, h, 16, 16)
-        exp_t.append(t + base - raster.tiles_of(cams[i], rz.params))
-        exp_rr.append(rr_ + i * n)
     ok, ov = np.concatenate(exp_k), np.concatenate(exp_v)
     keys, vals, ranges, K = _dupsort(rz, proj, 3 * n, cams, cap=len(ok))
     rz.check_status()
-    _check_lists(keys, vals, ranges, ok, ov, np.concatenate(exp_t), np.concatenate(exp_rr))
+    assert np.array_equal(keys, ok) and np.array_equal(vals, ov)
+    shifted, before = [], 0
+    for k, r in zip(exp_k, exp_r):
+        rr = r.copy()
+        nz = rr[:, 1] > rr[:, 0]
+        rr[nz] += before
+        shifted.append(rr)
+        before += len(k)
+    assert np.array_equal(ranges, np.concatenate(shifted))
 
 
 # ------------------------------------------------------------------ a1

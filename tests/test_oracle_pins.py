@@ -490,3 +490,30 @@ def test_touch_pairs_are_the_tiles_holding_support_pixels(tw, th):
     got = set(zip(t.tolist(), r.tolist()))
     assert got == exp
     assert 0 < len(got) < len(ok)
+
+
+@pytest.mark.parametrize("tw,th", [(16, 16), (8, 8), (32, 16)])
+def test_reach_lists_between_touched_pairs_and_boxes(tw, th):
+    """The binary32 reach rule of the tile lists is conservative and tight:
+    its lists hold every pair whose tile has a pixel centre in the support
+    ellipse (brute force, FP64), lie inside the support-box lists in the same
+    order, and drop box corners the ellipses miss."""
+    W, H = 300, 200
+    rec = scenes.random_records(3000, W, H, seed=17, max_ext=40.0)
+    dkey = np.where(rec["visible"], rec["depth"].view(np.uint32), np.uint32(0xFFFFFFFF)).astype(np.uint32)
+    foot = np.concatenate([rec["mean2d"], rec["ext"]], 1)
+    k, v, _ = oracle.dupsort_f32(foot, dkey, W, H, tw, th, chol=rec["chol"], rho2=rec["rho2"])
+    bk, bv, _ = oracle.dupsort_f32(foot, dkey, W, H, tw, th)
+    l00, l01, l11 = (rec["chol"][:, i].astype(np.float64) for i in range(3))
+    conic = np.stack([l00 * l00, l00 * l01, l01 * l01 + l11 * l11], 1)
+    t, r = oracle.touch_pairs(foot, dkey, conic, rec["rho2"].astype(np.float64), W, H, tw, th, 1.0)
+    R1 = np.int64(3001)
+    gid = k.astype(np.int64) * R1 + v
+    bid = bk.astype(np.int64) * R1 + bv
+    mask = np.isin(bid, gid)
+    assert np.array_equal(bid[mask], gid)
+    assert np.isin(t.astype(np.int64) * R1 + r, gid).all()
+    assert len(t) <= len(k) < 0.95 * len(bk)
+    # tight: boxes of one or two tiles are taken whole and the test is against
+    # the rectangle of pixel centres, yet the lists stay near the pixel-exact set
+    assert len(k) < 1.25 * len(t)
