@@ -137,7 +137,7 @@ DupWs dup_layout(char* base, int64_t R, int64_t cap, int key_passes) {
   w.dk_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
   w.dv_b = reinterpret_cast<uint32_t*>(take(4 * Rz));
   w.rect = reinterpret_cast<uint2*>(take(8 * Rz));
-  w.warp_counts = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
+  w.warp_counts = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_count_words((int64_t)Rz)));
   w.warp_tbase = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
   w.n_valid = reinterpret_cast<int64_t*>(take(8));
   w.k_alt = reinterpret_cast<uint32_t*>(take(4 * Cz));
@@ -546,8 +546,8 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
   w.x16 = take(2 * LS_MLP_IN * tiles);
   w.y = reinterpret_cast<float*>(take(4 * tiles));
   w.dstar_bits = reinterpret_cast<uint32_t*>(take(4 * tiles));
-  w.wc_kept = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
-  w.wc_held = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
+  w.wc_kept = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_count_words((int64_t)Rz)));
+  w.wc_held = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_count_words((int64_t)Rz)));
   w.warp_tbase = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
   w.k_keys = reinterpret_cast<uint32_t*>(take(4 * Cz));
   w.k_vals = reinterpret_cast<uint32_t*>(take(4 * Cz));
@@ -562,7 +562,7 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
   w.h_ranges = reinterpret_cast<int32_t*>(take(8 * tiles));
   // cleared before every call
   w.zero_begin = off;
-  w.diff = reinterpret_cast<int*>(take((32 * 8 + 4) * (size_t)(tiles_x + 1) * (tiles_y + 1)));  // coverage planes
+  w.diff = reinterpret_cast<int*>(take(33 * 4 * (size_t)(tiles_x + 1) * (tiles_y + 1)));  // coverage planes
   w.refuted = reinterpret_cast<uint8_t*>(take(tiles));
   w.has_held = reinterpret_cast<uint8_t*>(take(tiles));
   w.tmp_ctr_kept = reinterpret_cast<unsigned long long*>(take(8));

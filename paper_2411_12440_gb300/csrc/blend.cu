@@ -2,9 +2,13 @@
 // adjoint (Sec. 3.1 Eq. 6; kernel of Sec. 3.2 Eq. 11 with the alignment of
 // Sec. 3.3.1 Eq. 12; adaptive gradient scaling of Sec. 3.3.2 Eq. 13-14).
 //
-// One CTA per tile; each thread owns a 1 x PPT strip of pixels in one row, so
-// one shared-memory read of a record serves PPT pixels and the per-record
-// terms that depend only on the row (dy, l01 dy, l11 dy) are computed once.
+// One CTA per tile; each thread owns PPT pixels of one row, tile_w / PPT
+// apart, so one shared-memory read of a record serves PPT pixels and the
+// per-record terms that depend only on the row (dy, l01 dy, l11 dy) are
+// computed once.  A warp's p-th pixels then form a compact block (8 x 4 for
+// 16 x 16 tiles), so the per-pixel work, which runs once per p for the lanes
+// whose p-th pixel takes the record, wastes fewer lanes than with contiguous
+// strips (whose p-th pixels are 4 columns apart).
 // The tile's sorted record ids are walked in batches: the threads gather the
 // batch's 48-byte records into shared memory (each record is fetched from
 // L2/HBM once per tile), then every thread reads them as broadcasts.
@@ -80,7 +84,7 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
                                          int32_t* __restrict__ n_last, unsigned long long* stats,
                                          const TruncArgs& ta, int tile_gid) {
   const int sx = P.tile_w / PPT;
-  const int lr = (int)threadIdx.x / sx, lc = ((int)threadIdx.x % sx) * PPT;
+  const int lr = (int)threadIdx.x / sx, lc = (int)threadIdx.x % sx;
   const int py = J.y0 + lr, px0 = J.x0 + lc;
   const float y = (float)py + 0.5f;
   float xs[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
@@ -90,15 +94,15 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
   if (MODE == FWD_RESUME) ofs = ta.kept_ranges[tile_gid].y - ta.kept_ranges[tile_gid].x;
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
-    xs[p] = (float)(px0 + p) + 0.5f;
+    xs[p] = (float)(px0 + p * sx) + 0.5f;
     T[p] = 1.f;
     C0[p] = C1[p] = C2[p] = 0.f;
     last[p] = 0;
     comp[p] = 0;
-    const bool inside = px0 + p < J.W && py < J.H;
+    const bool inside = px0 + p * sx < J.W && py < J.H;
     if (!inside) done |= 1u << p;
     if (MODE == FWD_RESUME && inside) {
-      const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p;
+      const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p * sx;
       C0[p] = image[3 * pi];
       C1[p] = image[3 * pi + 1];
       C2[p] = image[3 * pi + 2];
@@ -130,8 +134,8 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
         const float l01dy = __fmul_rn(a.w, dy);
         const float e2 = __fmul_rn(bb.x, dy);
         const float e2s = __fmul_rn(e2, e2);
-        // q = fma(e1, e1, e2s) >= e2s for every pixel of the row: the whole
-        // strip is outside the support when the row term alone is
+        // q = fma(e1, e1, e2s) >= e2s for every pixel of the row: all of the
+        // thread's pixels are outside the support when the row term alone is
         if (e2s > bb.z) continue;
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
@@ -174,8 +178,8 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
   }
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
-    if (px0 + p < J.W && py < J.H) {
-      const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p;
+    if (px0 + p * sx < J.W && py < J.H) {
+      const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p * sx;
       if (raw) {
         image[3 * pi] = C0[p];
         image[3 * pi + 1] = C1[p];
@@ -204,7 +208,7 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
     int emax = 0, npix = 0, cc = 0;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-      if (px0 + p < J.W && py < J.H) {
+      if (px0 + p * sx < J.W && py < J.H) {
         emax = max(emax, stop[p] < n ? stop[p] + 1 : n);
         ++npix;
         cc += comp[p];
@@ -213,7 +217,7 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
     int never = 0;  // a pixel that never stopped
 #pragma unroll
     for (int p = 0; p < PPT; ++p)
-      if (px0 + p < J.W && py < J.H && stop[p] >= n) never = 1;
+      if (px0 + p * sx < J.W && py < J.H && stop[p] >= n) never = 1;
     atomicMax(&s_emax, emax);
     atomicAdd(&s_npix, npix);
     atomicAdd(&s_contrib, (unsigned long long)cc);
@@ -320,7 +324,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
                                          float* __restrict__ g2d) {
   const unsigned FULL = 0xffffffffu;
   const int sx = P.tile_w / PPT;
-  const int lr = (int)threadIdx.x / sx, lc = ((int)threadIdx.x % sx) * PPT;
+  const int lr = (int)threadIdx.x / sx, lc = (int)threadIdx.x % sx;
   const int py = J.y0 + lr, px0 = J.x0 + lc;
   const float y = (float)py + 0.5f;
   const int lane = threadIdx.x & 31;
@@ -329,12 +333,12 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
   int my_max = 0;
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
-    xs[p] = (float)(px0 + p) + 0.5f;
+    xs[p] = (float)(px0 + p * sx) + 0.5f;
     T[p] = Tf[p] = 1.f;
     gC0[p] = gC1[p] = gC2[p] = gTT[p] = 0.f;
     last[p] = 0;
-    if (px0 + p < J.W && py < J.H) {
-      const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p;
+    if (px0 + p * sx < J.W && py < J.H) {
+      const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p * sx;
       T[p] = Tf[p] = t_final[pi];
       last[p] = n_last[pi];
       gC0[p] = grad_image[3 * pi];
@@ -376,12 +380,12 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
       const float l01dy = __fmul_rn(a.w, dy);
       const float e2 = __fmul_rn(bb.x, dy);
       const float e2s = __fmul_rn(e2, e2);
-      // per-strip sums: the geometric terms are gathered as sums over the
-      // strip's pixels of gq e1, gq dx, gq dx^2 and gq (dy and l11 dy are the
-      // same for the whole strip) and expanded once per record below
+      // per-thread sums: the geometric terms are gathered as sums over the
+      // thread's pixels of gq e1, gq dx, gq dx^2 and gq (dy and l11 dy are the
+      // same for its whole row) and expanded once per record below
       float s_e1 = 0.f, s_dx = 0.f, s_dx2 = 0.f, s_q = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
       bool any = false;
-      const bool row_in = e2s <= bb.z;  // else q >= e2s > rho^2 for the whole strip
+      const bool row_in = e2s <= bb.z;  // else q >= e2s > rho^2 for the whole row
 #pragma unroll
       for (int p = 0; p < PPT; ++p) {
         if (!row_in) break;

@@ -20,8 +20,8 @@
 //               The learned path (learned.cu) uses the same kernel with the
 //               proposal depth (kept keys) and the refuted tiles (held-out
 //               keys) as extra conditions.
-//   dup_scan  : exclusive scan of the warp counts, total key count K and the
-//               capacity check.
+//   dup_reduce, dup_scan : exclusive scan of the warp counts, total key count
+//               K and the capacity check.
 #include "emit.cuh"
 #include "kernels.h"
 
@@ -53,71 +53,110 @@ __global__ void __launch_bounds__(DUP_THREADS) dup_count_kernel(int64_t R, const
   rect_sorted[j] = rc;
 }
 
-// One block scans the counts (exclusive, in place) in rounds of 8192: a
-// coalesced load into shared memory, 8 consecutive entries per thread (two
-// 16-byte shared loads), a block scan of the thread sums, and a coalesced
-// store.
-__global__ void __launch_bounds__(1024) dup_scan_kernel(int64_t n, uint32_t* counts, int64_t cap, int64_t* n_keys,
-                                                        int64_t* n_valid, int32_t* status) {
-  constexpr int PER = 8, ROUND = PER * 1024;
-  __shared__ __align__(16) uint32_t s_v[ROUND];
+// The scan of the warp counts in two launches over chunks of SCAN_CHUNK
+// counts, a block per chunk: dup_reduce sums each chunk; dup_scan adds up the
+// sums of the chunks before its own (the carry) and scans its chunk in place
+// (exclusive), 8 consecutive counts per thread.  The chunk sums sit behind
+// the counts, in the same buffer (enum_count_words).
+constexpr int SCAN_THREADS = 1024, SCAN_PER = 8, SCAN_CHUNK = SCAN_THREADS * SCAN_PER;
+
+__device__ __forceinline__ uint64_t* scan_parts(uint32_t* counts, int64_t n) {
+  return reinterpret_cast<uint64_t*>(counts + ((n + 1) & ~(int64_t)1));
+}
+
+// The 8 counts of this thread in its chunk (zero past n).
+__device__ __forceinline__ void scan_load(const uint32_t* counts, int64_t n, int64_t b0, uint32_t (&v)[SCAN_PER]) {
+  const int64_t i0 = b0 + (int64_t)SCAN_PER * threadIdx.x;
+  if (i0 + SCAN_PER <= n) {  // 32-byte aligned: b0 and SCAN_PER * tid are multiples of 8 counts
+    const uint4* g = reinterpret_cast<const uint4*>(counts + i0);
+    const uint4 a = g[0], b = g[1];
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) v[k] = i0 + k < n ? counts[i0 + k] : 0u;
+  }
+}
+
+// Block sum of x (every thread gets it); s_warp holds 32 entries.
+__device__ __forceinline__ uint64_t block_sum(uint64_t x, uint64_t* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if (lane == 0) s_warp[warp] = x;
+  __syncthreads();
+  uint64_t t = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) dup_reduce_kernel(int64_t n, uint32_t* counts) {
   __shared__ uint64_t s_warp[32];
-  __shared__ uint64_t s_carry;
+  uint32_t v[SCAN_PER];
+  scan_load(counts, n, (int64_t)blockIdx.x * SCAN_CHUNK, v);
+  uint64_t x = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER; ++k) x += v[k];
+  x = block_sum(x, s_warp);
+  if (threadIdx.x == 0) scan_parts(counts, n)[blockIdx.x] = x;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) dup_scan_kernel(int64_t n, uint32_t* counts, int64_t cap,
+                                                                int64_t* n_keys, int64_t* n_valid, int32_t* status) {
+  __shared__ uint64_t s_warp[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_carry = 0;
-  for (int64_t b0 = 0; b0 < n; b0 += ROUND) {
-    const int m = (int)(n - b0 < ROUND ? n - b0 : ROUND);
-    for (int i = tid; i < ROUND; i += 1024) s_v[i] = i < m ? counts[b0 + i] : 0u;
-    __syncthreads();
-    uint32_t v[PER];
-    const uint4* s4 = reinterpret_cast<const uint4*>(s_v + PER * tid);
+  const int64_t b0 = (int64_t)blockIdx.x * SCAN_CHUNK;
+  uint64_t carry = 0;
+  if (blockIdx.x > 0) {
+    const uint64_t* part = scan_parts(counts, n);
+    for (int i = tid; i < (int)blockIdx.x; i += SCAN_THREADS) carry += part[i];
+    carry = block_sum(carry, s_warp);
+  }
+  uint32_t v[SCAN_PER];
+  scan_load(counts, n, b0, v);
+  uint64_t run = 0;
 #pragma unroll
-    for (int q = 0; q < PER / 4; ++q) {
-      const uint4 u = s4[q];
-      v[4 * q] = u.x;
-      v[4 * q + 1] = u.y;
-      v[4 * q + 2] = u.z;
-      v[4 * q + 3] = u.w;
-    }
-    uint64_t run = 0;
+  for (int k = 0; k < SCAN_PER; ++k) run += v[k];
+  uint64_t x = run;
 #pragma unroll
-    for (int k = 0; k < PER; ++k) run += v[k];
-    uint64_t x = run;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t u = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += u;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = s_warp[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t u = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += u;
+      const uint64_t u = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += u;
     }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      uint64_t w = s_warp[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t u = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += u;
-      }
-      s_warp[lane] = w;
-    }
-    __syncthreads();
-    const uint64_t carry = s_carry;
-    uint64_t ex = x - run + (warp > 0 ? s_warp[warp - 1] : 0) + carry;
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const uint32_t c = v[k];
-      v[k] = (uint32_t)ex;
-      ex += c;
-    }
-    uint4* d4 = reinterpret_cast<uint4*>(s_v + PER * tid);
-#pragma unroll
-    for (int q = 0; q < PER / 4; ++q) d4[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    __syncthreads();
-    for (int i = tid; i < m; i += 1024) counts[b0 + i] = s_v[i];
-    if (tid == 1023) s_carry = ex;
-    __syncthreads();
+    s_warp[lane] = w;
   }
-  if (tid == 0) {
-    const uint64_t K = s_carry;
+  __syncthreads();
+  uint64_t ex = x - run + (warp > 0 ? s_warp[warp - 1] : 0) + carry;
+  const int64_t i0 = b0 + (int64_t)SCAN_PER * tid;
+  if (i0 + SCAN_PER <= n) {
+    uint32_t o[SCAN_PER];
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+      o[k] = (uint32_t)ex;
+      ex += v[k];
+    }
+    uint4* g = reinterpret_cast<uint4*>(counts + i0);
+    g[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    g[1] = make_uint4(o[4], o[5], o[6], o[7]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+      if (i0 + k < n) counts[i0 + k] = (uint32_t)ex;
+      ex += v[k];
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1 && tid == SCAN_THREADS - 1) {  // ex is now the total
+    const uint64_t K = ex;
     *n_keys = (int64_t)K;
     const bool fits = (int64_t)K <= cap;
     *n_valid = fits ? (int64_t)K : 0;
@@ -172,13 +211,19 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
     }
     return;  // block-uniform: nothing to do, or over capacity
   }
+  if (EMIT) {  // a block whose warps took no key has nothing to write
+    const int64_t g0 = (int64_t)blockIdx.x * ENUM_WARPS, g1 = g0 + ENUM_WARPS;
+    const uint64_t first = A.warp_counts[g0];
+    const uint64_t last = g1 < A.n_warps ? (uint64_t)A.warp_counts[g1] : (uint64_t)*A.n_valid;
+    if (last == first) return;  // block-uniform
+  }
   for (int c = tid; c < A.cams.n; c += ENUM_THREADS)
     s_cam[c] = CamLite{A.cams.c[c].W, A.cams.c[c].H, A.cams.c[c].tiles_x, A.cams.c[c].tile_base};
   const bool hist = A.tile_hist != nullptr;
   for (int i = tid; i < 3 * RADIX; i += ENUM_THREADS) (&s_hist[0][0])[i] = 0;
   __syncthreads();
   uint64_t out = 0;
-  bool walk = true;
+  bool walk = true, counted = false;  // counted: digits of keys written by this warp were counted
   if (EMIT) {
     out = A.out_base + (uint64_t)A.warp_counts[gw];
     const uint32_t tb = A.warp_tbase[gw];
@@ -260,6 +305,7 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
       tb = __shfl_sync(FULL, tb, 0);
     }
     const bool store = EMIT || tb != NO_STASH;
+    counted = store;
     uint32_t kept = 0, reached = 0;
     int sp = 0;  // record of the step's first row
     for (uint32_t cb = 0; cb < total; cb += 32) {
@@ -364,7 +410,8 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
     }
   }
   if (!hist) return;
-  __syncthreads();
+  // digits were counted only where keys were written here
+  if (!__syncthreads_or(counted)) return;
   for (int i = tid; i < A.key_passes * RADIX; i += ENUM_THREADS) {
     const uint32_t v = (&s_hist[0][0])[i];
     if (v) atomicAdd(&A.tile_hist[i], v);
@@ -383,8 +430,15 @@ cudaError_t launch_dup_count(int64_t R, const uint32_t* order, const uint32_t* d
 
 cudaError_t launch_dup_scan(int64_t n, uint32_t* counts, int64_t cap, int64_t* n_keys_dev, int64_t* n_valid_dev,
                             int32_t* status, cudaStream_t st) {
-  dup_scan_kernel<<<1, 1024, 0, st>>>(n, counts, cap, n_keys_dev, n_valid_dev, status);
+  const int64_t nb = n > 0 ? ceil_div(n, SCAN_CHUNK) : 1;
+  if (nb > 1) dup_reduce_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(n, counts);
+  dup_scan_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(n, counts, cap, n_keys_dev, n_valid_dev, status);
   return cudaGetLastError();
+}
+
+int64_t enum_count_words(int64_t R) {
+  const int64_t n = enum_warps(R);
+  return ((n + 1) & ~(int64_t)1) + 2 * (n > 0 ? ceil_div(n, SCAN_CHUNK) : 1);
 }
 
 int64_t enum_warps(int64_t R) { return R > 0 ? (int64_t)ceil_div(R, ENUM_BLOCK_RECS) * ENUM_WARPS : 0; }

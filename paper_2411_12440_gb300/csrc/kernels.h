@@ -80,8 +80,9 @@ constexpr int DUP_ITEMS = 2;
 constexpr int DUP_BLOCK = DUP_THREADS * DUP_ITEMS;
 cudaError_t launch_dup_count(int64_t R, const uint32_t* order, const uint32_t* dkey_sorted, const float4* foot,
                              const CamTable& cams, int n_per_cam, const ParDev& P, uint2* rect_sorted, cudaStream_t st);
-// Exclusive scan of n counts in place; *n_keys_dev = total, *n_valid_dev =
-// total when it fits cap (else 0, and LS_ERR_CAPACITY in *status).
+// Exclusive scan of n = enum_warps(R) counts in place (the buffer holds
+// enum_count_words(R) words); *n_keys_dev = total, *n_valid_dev = total when
+// it fits cap (else 0, and LS_ERR_CAPACITY in *status).
 cudaError_t launch_dup_scan(int64_t n, uint32_t* counts, int64_t cap, int64_t* n_keys_dev, int64_t* n_valid_dev,
                             int32_t* status, cudaStream_t st);
 
@@ -118,6 +119,9 @@ struct EnumArgs {
   uint8_t* has_held;              // ENUM_KEPT count launch: [tiles] set for tiles with keys beyond the proposal
 };
 int64_t enum_warps(int64_t R);
+// 32-bit words of a warp-count buffer for R records: the counts, then the
+// chunk sums of their scan.
+int64_t enum_count_words(int64_t R);
 cudaError_t launch_enum_keys(bool emit, int mode, const EnumArgs& A, cudaStream_t st);
 
 // ---- blending (blend.cu)

@@ -31,7 +31,10 @@ namespace ls {
 namespace {
 
 constexpr int NBINS = 32;
-constexpr float MASS_ONE = 16777216.f;  // fixed-point unit of the coverage planes
+// Fixed-point unit of the coverage planes: unsigned 32-bit sums are exact
+// modulo 2^32 whatever the order of the atomics, and every prefix sum that is
+// read (one bin's coverage of a tile, far below 2^15) fits.
+constexpr float MASS_ONE = 65536.f;
 
 __device__ __forceinline__ int depth_bin(float d, const DepthBins& B) {
   int b = 0;
@@ -54,7 +57,7 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(int64_t R, const float4*
                                                         const float4* __restrict__ foot,
                                                         const uint32_t* __restrict__ dkey, const CamDev cam,
                                                         const ParDev P, const DepthBins bins, int* __restrict__ count,
-                                                        long long* __restrict__ mass) {
+                                                        unsigned* __restrict__ mass) {
   extern __shared__ int s_count[];
   const int sx = cam.tiles_x + 1, cells = sx * (cam.tiles_y + 1);
   int* cnt = count;
@@ -73,20 +76,19 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(int64_t R, const float4*
     const float ellipse = 3.14159265f * b.z / fmaxf(a.z * b.x, 1e-30f);
     const float box = (float)((tx1 - tx0 + 1) * (ty1 - ty0 + 1) * P.tile_w * P.tile_h);
     const float w = b.y * (1.f / 3.f) * fminf(1.f, ellipse / box);
-    // fixed point (2^-24): integer sums do not depend on the order of the atomics
-    const long long wq = __float2ll_rn(w * MASS_ONE);
+    // fixed point: integer sums do not depend on the order of the atomics
+    const unsigned wq = (unsigned)__float2int_rn(w * MASS_ONE);
     if (COUNTS != HIST_NONE) {
       atomicAdd(&cnt[ty0 * sx + tx0], 1);
       atomicAdd(&cnt[ty0 * sx + tx1 + 1], -1);
       atomicAdd(&cnt[(ty1 + 1) * sx + tx0], -1);
       atomicAdd(&cnt[(ty1 + 1) * sx + tx1 + 1], 1);
     }
-    unsigned long long* d =
-        reinterpret_cast<unsigned long long*>(mass + (size_t)depth_bin(__uint_as_float(dk), bins) * cells);
-    atomicAdd(&d[ty0 * sx + tx0], (unsigned long long)wq);
-    atomicAdd(&d[ty0 * sx + tx1 + 1], (unsigned long long)-wq);
-    atomicAdd(&d[(ty1 + 1) * sx + tx0], (unsigned long long)-wq);
-    atomicAdd(&d[(ty1 + 1) * sx + tx1 + 1], (unsigned long long)wq);
+    unsigned* d = mass + (size_t)depth_bin(__uint_as_float(dk), bins) * cells;
+    atomicAdd(&d[ty0 * sx + tx0], wq);
+    atomicAdd(&d[ty0 * sx + tx1 + 1], 0u - wq);
+    atomicAdd(&d[(ty1 + 1) * sx + tx0], 0u - wq);
+    atomicAdd(&d[(ty1 + 1) * sx + tx1 + 1], wq);
   }
   if (COUNTS == HIST_PRIVATE) {
     __syncthreads();
@@ -138,13 +140,13 @@ __device__ __forceinline__ void prefix_plane(V* d, int sx, int sy) {
   }
 }
 
-__global__ void __launch_bounds__(256) hist_prefix_kernel(long long* __restrict__ mass, int* __restrict__ count, int sx,
+__global__ void __launch_bounds__(256) hist_prefix_kernel(unsigned* __restrict__ mass, int* __restrict__ count, int sx,
                                                           int sy) {
   if (blockIdx.x < NBINS) prefix_plane(mass + (size_t)blockIdx.x * sx * sy, sx, sy);
   else prefix_plane(count, sx, sy);
 }
 
-__global__ void __launch_bounds__(256) features_kernel(const long long* __restrict__ mass, const int* __restrict__ count,
+__global__ void __launch_bounds__(256) features_kernel(const unsigned* __restrict__ mass, const int* __restrict__ count,
                                                        const CamDev cam, const ParDev P, __half* __restrict__ x,
                                                        int32_t* __restrict__ tile_total,
                                                        unsigned long long* key_total) {
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(256) features_kernel(const long long* __restri
   // cumulative coverage in front of each bin's upper edge
   float cum = 0.f;
   for (int b = 0; b < NBINS; ++b) {
-    const long long m = mass[(size_t)b * plane + ty * sx + tx];
+    const int m = (int)mass[(size_t)b * plane + ty * sx + tx];  // exact: the true sum fits
     cum += m > 0 ? (float)m * (1.f / MASS_ONE) : 0.f;
     row[b] = __float2half_rn(log1pf(cum));
   }
@@ -223,13 +225,13 @@ DepthBins make_depth_bins() {
 }
 
 size_t hist_planes_bytes(const CamDev& cam) {
-  return (size_t)(NBINS * 8 + 4) * (cam.tiles_x + 1) * (cam.tiles_y + 1);
+  return (size_t)(NBINS + 1) * 4 * (cam.tiles_x + 1) * (cam.tiles_y + 1);
 }
 
 cudaError_t launch_tile_hist(int64_t R, const float4* rec, const float4* foot, const uint32_t* dkey,
                              const CamDev& cam, const ParDev& P, void* planes, bool counts, cudaStream_t st) {
   if (R == 0) return cudaSuccess;
-  long long* mass = static_cast<long long*>(planes);
+  unsigned* mass = static_cast<unsigned*>(planes);
   int* count = reinterpret_cast<int*>(mass + (size_t)NBINS * (cam.tiles_x + 1) * (cam.tiles_y + 1));
   const size_t plane = sizeof(int) * (size_t)(cam.tiles_x + 1) * (cam.tiles_y + 1);
   if (!counts) {
@@ -255,7 +257,7 @@ cudaError_t launch_tile_hist(int64_t R, const float4* rec, const float4* foot, c
 
 cudaError_t launch_features(void* planes, const CamDev& cam, const ParDev& P, void* x, int32_t* tile_total,
                             unsigned long long* key_total, cudaStream_t st) {
-  long long* mass = static_cast<long long*>(planes);
+  unsigned* mass = static_cast<unsigned*>(planes);
   int* count = reinterpret_cast<int*>(mass + (size_t)NBINS * (cam.tiles_x + 1) * (cam.tiles_y + 1));
   // the count plane is prefixed only when its totals are wanted
   hist_prefix_kernel<<<tile_total ? NBINS + 1 : NBINS, 256, 0, st>>>(mass, count, cam.tiles_x + 1, cam.tiles_y + 1);

@@ -5,8 +5,9 @@
 // duplication output by tile id keeps each tile's entries in the depth order
 // they were emitted in: the front-to-back order of Sec. 3.1 Eq. 6.
 //
-// Per pass every partition of SORT_PART keys is claimed with an atomic ticket
-// (so a partition only ever waits on partitions that are already running),
+// Per pass a persistent grid claims the partitions of SORT_PART keys with an
+// atomic ticket (so a partition only ever waits on partitions that are
+// already running, and no block is launched for capacity that holds no keys),
 // ranked in registers with warp ballots, published as a per-digit aggregate,
 // completed by looking back over its predecessors, staged in shared memory in
 // sorted order and written out in digit runs.  Every wait on a predecessor is
@@ -116,13 +117,16 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
   OnesweepSmem<PART>& S = *reinterpret_cast<OnesweepSmem<PART>*>(smem_raw);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t n = n_dev ? *n_dev : n_host;
+  // persistent: the block takes partitions by ticket until none is left
+  for (;;) {
+  __syncthreads();  // the previous partition is done with shared memory
   for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&S.whist[0][0])[i] = 0;
   if (tid == 0) S.part = atomicAdd(part_ctr, 1u);
   __syncthreads();
-  const int64_t n = n_dev ? *n_dev : n_host;
   const uint32_t part = S.part;
   const int64_t base = (int64_t)part * PART;
-  if (base >= n) return;  // block-uniform
+  if (base >= n) break;  // block-uniform
   const int n_in = (int)(n - base < PART ? n - base : PART);
 
   // values: asynchronous copy into shared memory, in flight during ranking
@@ -229,6 +233,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
       }
     }
   }
+  }  // partitions
 }
 
 // Ranges were accumulated as (min start, ~max end) from 0xFFFFFFFF; empty
@@ -293,7 +298,16 @@ static cudaError_t onesweep_launch(const uint32_t* keys_in, const uint32_t* vals
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  unsigned grid = ceil_div(cap > 0 ? cap : 1, PART);
+  // persistent grid: as many blocks as fit at once (four per SM), or fewer
+  // when the capacity needs fewer partitions
+  static int sms[64] = {0};
+  if (dev >= 0 && dev < 64 && sms[dev] == 0) {
+    e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t parts = (cap > 0 ? cap + PART - 1 : PART) / PART;
+  const int64_t resident = (dev >= 0 && dev < 64 ? sms[dev] : 152) * 4;
+  const unsigned grid = (unsigned)(parts < resident ? parts : resident);
   onesweep_kernel<BITS, ITEMS><<<grid, SORT_THREADS, sm, st>>>(
       keys_in, vals_in, keys_out, vals_out, n_dev, n_host, shift, s.hist + (size_t)pass * RADIX,
       s.lookback + (size_t)pass * s.parts * RADIX, s.part_ctr + pass, reinterpret_cast<uint2*>(ranges), status);
