@@ -671,7 +671,10 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
     LS_TRY(launch_dup_count(R, w.dv_a, w.dk_a, pp.foot, T, n, P, w.rect, st));
   }
   // per-tile features and the proposal
-  LS_TRY(launch_tile_hist(R, pp.rec, pp.foot, pp.dkey, C, P, w.diff, false, st));
+  if (tile_hist_sorted_smem(C) <= 160 * 1024)
+    LS_TRY(launch_tile_hist_sorted(R, w.dv_a, w.dk_a, w.rect, pp.rec, C, P, w.diff, st));
+  else
+    LS_TRY(launch_tile_hist(R, pp.rec, pp.foot, pp.dkey, C, P, w.diff, false, st));
   LS_TRY(launch_features(w.diff, C, P, w.x16, nullptr, nullptr, st));
   if (mlp) LS_TRY(launch_mlp_forward(tiles, w.x16, mlp_dev(mlp), w.y, st));
   LS_TRY(launch_dstar(tiles, mlp ? w.y : nullptr, margin, dstar_in, w.dstar_bits, dstar_out, st));

@@ -328,7 +328,10 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
   const int py = J.y0 + lr, px0 = J.x0 + lc;
   const float y = (float)py + 0.5f;
   const int lane = threadIdx.x & 31;
-  float xs[PPT], T[PPT], Tf[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gTT[PPT], S0[PPT], S1[PPT], S2[PPT];
+  // GS = dL/dC . S + dL/dT_final T_final, where S is the colour composited
+  // behind the current entry (background included): the part of dL/dalpha
+  // that the entries behind contribute, kept as one running scalar
+  float xs[PPT], T[PPT], Tf[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gTT[PPT], GS[PPT];
   int last[PPT];
   int my_max = 0;
 #pragma unroll
@@ -346,9 +349,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
       gC2[p] = grad_image[3 * pi + 2];
       gTT[p] = grad_t ? grad_t[pi] * Tf[p] : 0.f;  // dL/dT_final times T_final
     }
-    S0[p] = P.bg[0] * Tf[p];
-    S1[p] = P.bg[1] * Tf[p];
-    S2[p] = P.bg[2] * Tf[p];
+    GS[p] = (gC0[p] * P.bg[0] + gC1[p] * P.bg[1] + gC2[p] * P.bg[2]) * Tf[p] + gTT[p];
     my_max = max(my_max, last[p]);
   }
   if (threadIdx.x == 0) *s_max = 0;
@@ -386,6 +387,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
       float s_e1 = 0.f, s_dx = 0.f, s_dx2 = 0.f, s_q = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
       bool any = false;
       const bool row_in = e2s <= bb.z;  // else q >= e2s > rho^2 for the whole row
+      const float kq = 0.5f * bb.y * P.inv_lambda;
 #pragma unroll
       for (int p = 0; p < PPT; ++p) {
         if (!row_in) break;
@@ -403,18 +405,18 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
         v6 += wgt * gC0[p];
         v7 += wgt * gC1[p];
         v8 += wgt * gC2[p];
-        const float ga = gC0[p] * (c.x * Tb - S0[p] * iom) + gC1[p] * (c.y * Tb - S1[p] * iom) +
-                         gC2[p] * (c.z * Tb - S2[p] * iom) - gTT[p] * iom;
-        S0[p] += c.x * wgt;
-        S1[p] += c.y * wgt;
-        S2[p] += c.z * wgt;
+        // dL/dalpha = Tb dL/dC . c - (dL/dC . S + dL/dT_final T_final) / (1 - alpha)
+        const float gcd = gC0[p] * c.x + gC1[p] * c.y + gC2[p] * c.z;
+        const float ga = Tb * gcd - iom * GS[p];
+        GS[p] += wgt * gcd;
         T[p] = Tb;
         if (araw <= P.alpha_max) {
           v5 += f * ga;
-          float gD = bb.y * ga * kern_df<KID>(xk) * P.inv_lambda;
+          // dL/dq = dL/dalpha o f'(x) / (lambda 2 D), o / (2 lambda) per record
+          float gD = ga * kern_df<KID>(xk) * kq;
           if (P.ags == 1) gD *= __expf(-D * D);
           else if (P.ags == 2) gD *= __expf(-xk * xk);
-          const float gq = D > 0.f ? 0.5f * __fdividef(gD, D) : 0.f;
+          const float gq = D > 0.f ? __fdividef(gD, D) : 0.f;
           const float gdx = gq * dx;
           s_e1 += gq * e1;
           s_dx += gdx;

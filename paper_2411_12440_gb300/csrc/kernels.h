@@ -167,6 +167,13 @@ size_t hist_planes_bytes(const CamDev& cam);
 // counts = false leaves out the plane of box counts (no tile totals wanted).
 cudaError_t launch_tile_hist(int64_t R, const float4* rec, const float4* foot, const uint32_t* dkey,
                              const CamDev& cam, const ParDev& P, void* planes, bool counts, cudaStream_t st);
+// The coverage planes only (no count plane) from the depth order: order,
+// sorted depth keys and the support boxes of dup_count (rect_sorted).  The
+// shared plane of tile_hist_sorted_smem(cam) bytes must fit one block.
+size_t tile_hist_sorted_smem(const CamDev& cam);
+cudaError_t launch_tile_hist_sorted(int64_t R, const uint32_t* order, const uint32_t* dkey_sorted,
+                                    const uint2* rect_sorted, const float4* rec, const CamDev& cam, const ParDev& P,
+                                    void* planes, cudaStream_t st);
 cudaError_t launch_features(void* planes, const CamDev& cam, const ParDev& P, void* x, int32_t* tile_total,
                             unsigned long long* key_total, cudaStream_t st);
 cudaError_t launch_dstar(int ntiles, const float* y, float margin, const float* dstar_in, uint32_t* bits,

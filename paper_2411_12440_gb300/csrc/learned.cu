@@ -97,6 +97,88 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(int64_t R, const float4*
   }
 }
 
+// The coverage planes from the depth order: records of one depth bin are
+// contiguous there, so each block takes a contiguous range of the sorted
+// records, accumulates the plane of the bin at hand in shared memory, and
+// adds it to the global plane (nonzero cells only) when the bin changes and
+// at the end: shared-memory atomics per record, a few plane flushes per
+// block.  Same weights and fixed point as tile_hist_kernel, so the planes are
+// the same bit for bit.  Dynamic shared memory: one plane of unsigned cells.
+constexpr int HIST_SORTED_THREADS = 512;
+
+__device__ __forceinline__ void flush_plane(unsigned* __restrict__ s_plane, unsigned* __restrict__ g_plane,
+                                            int cells) {
+  for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+    const unsigned v = s_plane[i];
+    if (v) {
+      atomicAdd(&g_plane[i], v);
+      s_plane[i] = 0u;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(HIST_SORTED_THREADS) tile_hist_sorted_kernel(
+    int64_t R, const uint32_t* __restrict__ order, const uint32_t* __restrict__ dkey_sorted,
+    const uint2* __restrict__ rect_sorted, const float4* __restrict__ rec, const CamDev cam, const ParDev P,
+    const DepthBins bins, unsigned* __restrict__ mass) {
+  extern __shared__ unsigned s_plane[];
+  __shared__ int s_bin[2];
+  const int sx = cam.tiles_x + 1, cells = sx * (cam.tiles_y + 1);
+  for (int i = threadIdx.x; i < cells; i += blockDim.x) s_plane[i] = 0u;
+  const int64_t per = (R + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < R ? lo + per : R;
+  int cur = -1;  // bin of the shared plane (block-uniform)
+  for (int64_t c0 = lo; c0 < hi; c0 += blockDim.x) {
+    const int64_t j = c0 + threadIdx.x;
+    int bin = -1;
+    unsigned wq = 0u;
+    uint2 rc = make_uint2(1u, 0u);
+    if (j < hi) {
+      const uint32_t dk = dkey_sorted[j];
+      rc = rect_sorted[j];
+      if (dk != DKEY_CULLED && (rc.x >> 16) >= (rc.x & 0xFFFFu)) {  // a non-empty box
+        const uint32_t r = order[j];
+        const float4 a = rec[3 * (size_t)r], b = rec[3 * (size_t)r + 1];  // {mx, my, l00, l01}, {l11, o, rho2, depth}
+        const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+        const float ellipse = 3.14159265f * b.z / fmaxf(a.z * b.x, 1e-30f);
+        const float box = (float)((tx1 - tx0 + 1) * (ty1 - ty0 + 1) * P.tile_w * P.tile_h);
+        const float w = b.y * (1.f / 3.f) * fminf(1.f, ellipse / box);
+        wq = (unsigned)__float2int_rn(w * MASS_ONE);
+        bin = depth_bin(__uint_as_float(dk), bins);
+      }
+    }
+    // bins rise with the depth order: the chunk's bins are [first, last] of
+    // its binned records
+    if (threadIdx.x == 0) s_bin[0] = NBINS, s_bin[1] = -1;
+    __syncthreads();
+    if (bin >= 0) {
+      atomicMin(&s_bin[0], bin);
+      atomicMax(&s_bin[1], bin);
+    }
+    __syncthreads();
+    const int b_first = s_bin[0], b_last = s_bin[1];
+    __syncthreads();  // s_bin is read before the next chunk resets it
+    for (int b = b_first; b <= b_last; ++b) {
+      if (b != cur) {
+        if (cur >= 0) {
+          flush_plane(s_plane, mass + (size_t)cur * cells, cells);
+          __syncthreads();
+        }
+        cur = b;
+      }
+      if (bin == b) {
+        const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+        atomicAdd(&s_plane[ty0 * sx + tx0], wq);
+        atomicAdd(&s_plane[ty0 * sx + tx1 + 1], 0u - wq);
+        atomicAdd(&s_plane[(ty1 + 1) * sx + tx0], 0u - wq);
+        atomicAdd(&s_plane[(ty1 + 1) * sx + tx1 + 1], wq);
+      }
+      __syncthreads();
+    }
+  }
+  if (cur >= 0) flush_plane(s_plane, mass + (size_t)cur * cells, cells);
+}
+
 // One block per plane (the 32 mass planes, then the count plane): prefix
 // along rows (a warp per row, coalesced warp scans), then along columns (a
 // thread per column, loads batched eight rows at a time).
@@ -252,6 +334,28 @@ cudaError_t launch_tile_hist(int64_t R, const float4* rec, const float4* foot, c
     tile_hist_kernel<HIST_GLOBAL><<<ceil_div(R, 256), 256, 0, st>>>(R, rec, foot, dkey, cam, P, make_depth_bins(),
                                                                     count, mass);
   }
+  return cudaGetLastError();
+}
+
+size_t tile_hist_sorted_smem(const CamDev& cam) {
+  return sizeof(unsigned) * (size_t)(cam.tiles_x + 1) * (cam.tiles_y + 1);
+}
+
+cudaError_t launch_tile_hist_sorted(int64_t R, const uint32_t* order, const uint32_t* dkey_sorted,
+                                    const uint2* rect_sorted, const float4* rec, const CamDev& cam, const ParDev& P,
+                                    void* planes, cudaStream_t st) {
+  if (R == 0) return cudaSuccess;
+  const size_t sm = tile_hist_sorted_smem(cam);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess && sm > 48 * 1024)
+    e = cudaFuncSetAttribute(tile_hist_sorted_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  // two blocks per SM, each with at least a few chunks of records
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 2, ceil_div(R, 8 * HIST_SORTED_THREADS)));
+  tile_hist_sorted_kernel<<<(unsigned)grid, HIST_SORTED_THREADS, sm, st>>>(
+      R, order, dkey_sorted, rect_sorted, rec, cam, P, make_depth_bins(), static_cast<unsigned*>(planes));
   return cudaGetLastError();
 }
 

@@ -100,6 +100,26 @@ def test_learned_render_is_exact_for_any_proposal(margin):
         assert refuted > 0 and held > 0
 
 
+def test_learned_proposals_follow_the_tile_features():
+    """The render's own coverage planes (accumulated in depth order) give the
+    same features as the standalone tile features (accumulated in record
+    order): the proposals are the network's output on them."""
+    scene, cam = _cluster(150_000, 5)
+    sp = raster.Splats.from_scene(scene)
+    P = raster.RenderParams(sh_degree=3)
+    rz = raster.Rasterizer(raster.RenderParams(sh_degree=3))
+    lr = LearnedRenderer(sp, cam, P)
+    net = TerminationMLP(scenes.random_mlp_params(7))
+    lr.render(net, margin=0.5)
+    proj, _ = rz.project(sp, [cam], counts=False)
+    x, _ = rz.tile_features(proj, sp.n, cam)
+    y = net.forward(x)
+    torch.cuda.synchronize()
+    lr.check()
+    expect = torch.exp(y + 0.5)
+    assert torch.allclose(lr.dstar, expect, rtol=1e-5, atol=0)
+
+
 @pytest.mark.parametrize("dstar", [0.0, math.inf])
 def test_learned_render_extremes(dstar):
     """Proposal 0 keeps nothing (every non-empty tile refuted and resumed);
