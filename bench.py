@@ -372,7 +372,9 @@ def bench_learned(dev, reps=20):
     if const is not None:
         modes["const"] = dict(dstar_in=torch.full((lr.tiles,), const, device=dev))
     for name, kw in modes.items():
-        ms = timed(lambda: lr.render(t_thr=t_thr, **kw))
+        ms = timed(lambda: lr.render(t_thr=t_thr, stats=False, **kw))
+        lr.check()
+        lr.render(t_thr=t_thr, **kw)  # once more with the counters
         lr.check()
         total, kept, held, refuted = lr.counters()
         out[name] = {"ms": ms, "keys_sorted": kept + held, "keys_kept": kept, "keys_held_sorted": held,

@@ -260,9 +260,11 @@ ls_status ls_tile_features(const void* proj, int64_t n_records, const ls_camera*
  * With t_thr <= params->t_min the image equals ls_render_fwd's bit for bit;
  * with a larger t_thr each pixel is within t_thr (max rgb + bg) of it.
  * Outputs as ls_render_fwd (n_last continues into the held-out lists),
- * dstar_out [tiles] (or NULL), stats_dev [4] (int64, device): keys before
- * truncation, kept keys, held-out keys sorted for refuted tiles, refuted
- * tiles.  key_capacity bounds both the kept and the held-out keys. */
+ * dstar_out [tiles] (or NULL), stats_dev [4] (int64, device, or NULL): keys
+ * before truncation, kept keys, held-out keys sorted for refuted tiles,
+ * refuted tiles (counting the keys before truncation walks the rows of
+ * records that lie beyond every proposal of their box, which NULL skips).
+ * key_capacity bounds both the kept and the held-out keys. */
 size_t ls_render_learned_workspace(int32_t n, const ls_camera* cam, const ls_params* params, int64_t key_capacity);
 ls_status ls_render_learned(int32_t n, const float* means, const float* scales, const float* quats,
                             const float* opacities, const float* sh, const ls_camera* cam, const ls_params* params,

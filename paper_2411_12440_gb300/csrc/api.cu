@@ -545,7 +545,7 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
   w.rect = reinterpret_cast<uint2*>(take(8 * Rz));
   w.x16 = take(2 * LS_MLP_IN * tiles);
   w.y = reinterpret_cast<float*>(take(4 * tiles));
-  w.dstar_bits = reinterpret_cast<uint32_t*>(take(4 * tiles));
+  w.dstar_bits = reinterpret_cast<uint32_t*>(take(4 * (size_t)dstar_pyramid_words(tiles_x, tiles_y)));  // + pyramid
   w.wc_kept = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_count_words((int64_t)Rz)));
   w.wc_held = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_count_words((int64_t)Rz)));
   w.warp_tbase = reinterpret_cast<uint32_t*>(take(4 * (size_t)enum_warps((int64_t)Rz)));
@@ -642,7 +642,7 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   int64_t tiles64 = 0;
   if (!make_cams(cam, 1, params, T, &tiles64)) return LS_ERR_INVALID_ARG;
   if (key_capacity < 0 || key_capacity > 0x7FFFFFFFll) return LS_ERR_INVALID_ARG;
-  if (!image || !t_final || !n_last || !stats_dev || !workspace) return LS_ERR_INVALID_ARG;
+  if (!image || !t_final || !n_last || !workspace) return LS_ERR_INVALID_ARG;
   if (mlp ? !mlp_ok(mlp) : !dstar_in) return LS_ERR_INVALID_ARG;
   if (n > 0 && (!means || !scales || !quats || !opacities || !sh)) return LS_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(quats) % 16 || reinterpret_cast<uintptr_t>(workspace) % 256)
@@ -677,7 +677,7 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
     LS_TRY(launch_tile_hist(R, pp.rec, pp.foot, pp.dkey, C, P, w.diff, false, st));
   LS_TRY(launch_features(w.diff, C, P, w.x16, nullptr, nullptr, st));
   if (mlp) LS_TRY(launch_mlp_forward(tiles, w.x16, mlp_dev(mlp), w.y, st));
-  LS_TRY(launch_dstar(tiles, mlp ? w.y : nullptr, margin, dstar_in, w.dstar_bits, dstar_out, st));
+  LS_TRY(launch_dstar(C, mlp ? w.y : nullptr, margin, dstar_in, w.dstar_bits, dstar_out, w.diff, w.has_held, st));
   // kept keys: count per warp (and every key the ellipses reach), scan,
   // emit, sort, blend
   SortScratch ks = sort_scratch_carve(w.kept_scratch, key_capacity > 0 ? key_capacity : 1, kp);
@@ -705,8 +705,9 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
     ea.dshift[p] = td.shift[p];
     ea.dmask[p] = (1u << td.bits[p]) - 1u;
   }
-  ea.key_total = w.key_total;
-  ea.has_held = w.has_held;
+  ea.key_total = stats_dev ? w.key_total : nullptr;  // counting every reached key only for the stats
+  ea.dstar_pyr = w.dstar_bits;
+  ea.pyr = make_dstar_pyramid(C.tiles_x, C.tiles_y);
   ea.warp_counts = w.wc_kept;
   ea.warp_tbase = w.warp_tbase;
   ea.n_warps = enum_warps(R);
@@ -759,7 +760,7 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   }
   LS_TRY(launch_blend_trunc(2, pp.rec, C, P, reinterpret_cast<const int2*>(w.h_ranges), w.h_vals, image, t_final,
                             n_last, ta, st));
-  LS_TRY(launch_learned_stats(w.key_total, w.n_kept, w.n_held, w.n_refuted, stats_dev, st));
+  if (stats_dev) LS_TRY(launch_learned_stats(w.key_total, w.n_kept, w.n_held, w.n_refuted, stats_dev, st));
   return LS_OK;
 }
 

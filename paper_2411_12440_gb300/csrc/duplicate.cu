@@ -166,17 +166,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) dup_scan_kernel(int64_t n, uint3
 
 // The condition of each mode on a key its record reaches (depth bits dk):
 // ENUM_ALL none; ENUM_KEPT depth bits <= the tile's proposal; ENUM_HELD the
-// tile is refuted and the depth is beyond its proposal.  In the count launch
-// of ENUM_KEPT a reached key beyond the proposal flags its tile in has_held.
-template <int MODE, bool COUNT>
+// tile is refuted and the depth is beyond its proposal.
+template <int MODE>
 __device__ __forceinline__ bool key_taken(const EnumArgs& A, uint32_t dk, uint32_t key) {
   if (MODE == ENUM_ALL) return true;
   const uint32_t lim = __ldg(A.dstar_bits + key);
-  if (MODE == ENUM_KEPT) {
-    const bool kept = dk <= lim;
-    if (COUNT && !kept && !__ldg(A.has_held + key)) A.has_held[key] = 1;
-    return kept;
-  }
+  if (MODE == ENUM_KEPT) return dk <= lim;
   return A.refuted[key] && dk > lim;
 }
 
@@ -188,12 +183,14 @@ constexpr uint32_t NO_STASH = 0xFFFFFFFFu;
 // counts the taken keys (warp_counts) and, when the whole box-tile count of
 // its records fits in the stash (tmp_*, bump-allocated per warp), also
 // writes them there, compacted (warp_tbase; NO_STASH otherwise), with their
-// tile-sort digits.  ENUM_KEPT also adds every reached key to *key_total and
-// flags tiles in has_held.  Emit launch (EMIT = true), after the counts are
-// scanned into offsets: a stashed warp copies its keys to its offset; any
-// other warp walks again and writes them (and their digits).  ENUM_HELD
-// drops up front every record whose box holds no refuted tile (summed-area
-// table `sat`).
+// tile-sort digits.  ENUM_KEPT takes no key of a record that lies beyond the
+// proposal bound of its whole box; when key_total is given, it adds every
+// reached key to it (walking such a record's rows for the count only),
+// else it drops such records up front.  Emit launch (EMIT =
+// true), after the counts are scanned into offsets: a stashed warp copies
+// its keys to its offset; any other warp walks again and writes them (and
+// their digits).  ENUM_HELD drops up front every record whose box holds no
+// refuted tile (summed-area table `sat`).
 template <bool EMIT, int MODE>
 __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
   __shared__ EnumRec S[ENUM_WARPS][ENUM_WARP_RECS];
@@ -277,8 +274,16 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
         if (sat[(y1 + 1) * sx + x1 + 1] - sat[y0 * sx + x1 + 1] - sat[(y1 + 1) * sx + x0] + sat[y0 * sx + x0] == 0)
           rc = make_uint2(1u, 0u);
       }
+      // ENUM_KEPT: a record beyond the proposal bound of its whole box takes
+      // no key; it is walked only to count its reached keys (*key_total)
+      bool beyond = false;
+      if (MODE == ENUM_KEPT && box_rows(rc)) {
+        beyond = dk > box_dstar_bound(A.dstar_pyr, A.pyr, (int)(rc.x & 0xFFFF), (int)(rc.x >> 16),
+                                      (int)(rc.y & 0xFFFF), (int)(rc.y >> 16));
+        if (beyond && (EMIT || !A.key_total)) rc = make_uint2(1u, 0u);
+      }
       const uint32_t rows = box_rows(rc);
-      uint32_t x = rows, bx = box_count(rc);
+      uint32_t x = rows, bx = beyond ? 0u : box_count(rc);
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t u = __shfl_up_sync(FULL, x, o);
@@ -288,7 +293,9 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
       const unsigned nz = __ballot_sync(FULL, rows > 0);
       if (rows) {
         const CamLite cm = s_cam[A.cams.n > 1 ? r / (uint32_t)A.n_per_cam : 0u];
-        enum_rec(W[n_nz + __popc(nz & lt)], total + x - rows, rc, r, dk, cm, A.rec);
+        EnumRec& t = W[n_nz + __popc(nz & lt)];
+        enum_rec(t, total + x - rows, rc, r, dk, cm, A.rec);
+        if (MODE == ENUM_KEPT) t.beyond = beyond;
       }
       n_nz += __popc(nz);
       total += __shfl_sync(FULL, x, 31);
@@ -333,9 +340,13 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
         }
         r = g3.x;
         dk = g3.y;
+        if (MODE == ENUM_KEPT && g3.z) {  // beyond every proposal of its box: reached, none taken
+          reached += n;
+          n = 0;
+        }
       }
       sp = __shfl_sync(FULL, sl, 31);
-      // this step's rows with keys, compacted, and the walk over their keys
+      // this step's rows with keys to walk, compacted, and the walk over their keys
       uint32_t xs = n;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -364,7 +375,7 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
           const uint4 rw = SRw[sj];
           key = rw.x + (e2 - rw.y);
           rr = rw.z;
-          take = key_taken<MODE, !EMIT>(A, rw.w, key);
+          take = key_taken<MODE>(A, rw.w, key);
         }
         sq = __shfl_sync(FULL, sj, 31);
         const unsigned bal = __ballot_sync(FULL, take);
@@ -398,14 +409,14 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
       __syncwarp();  // the rows of this step are read before the next step rewrites them
     }
     if (!EMIT) {
-      if (MODE == ENUM_KEPT) {
+      if (MODE == ENUM_KEPT && A.key_total) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) reached += __shfl_xor_sync(FULL, reached, o);
       }
       if (lane == 0) {
         A.warp_counts[gw] = kept;
         A.warp_tbase[gw] = tb;
-        if (MODE == ENUM_KEPT && reached) atomicAdd(A.key_total, (unsigned long long)reached);
+        if (MODE == ENUM_KEPT && A.key_total && reached) atomicAdd(A.key_total, (unsigned long long)reached);
       }
     }
   }

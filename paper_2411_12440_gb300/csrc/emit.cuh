@@ -46,7 +46,8 @@ struct __align__(16) EnumRec {
   float dyl;             // dy of the leftmost point of D^2 = L
   float ext_y;           // half height of D^2 = L: sqrt(L) / l11
   uint32_t r, dk;        // record id, depth bits
-  uint32_t pad0, pad1;
+  uint32_t beyond;       // ENUM_KEPT: the record lies beyond every proposal of its box (takes no key)
+  uint32_t pad1;
 };
 
 __device__ __forceinline__ uint32_t box_count(uint2 rc) {
@@ -92,6 +93,19 @@ __device__ __forceinline__ void enum_rec(EnumRec& t, uint32_t off, uint2 rc, uin
   const float nrm = __fsqrt_rn(__fmaf_rn(b.x, b.x, __fmul_rn(a.w, a.w)));
   reinterpret_cast<float4*>(&t)[2] =
       make_float4(b.x, L, __fdiv_rn(__fmul_rn(sL, a.w), __fmul_rn(b.x, nrm)), __fdiv_rn(sL, b.x));
+}
+
+// An upper bound of the proposal bits over the tile box [x0, x1] x [y0, y1]:
+// the max of the (at most 2 x 2) cells of the first pyramid level at which
+// the box spans at most two cells each way.
+__device__ __forceinline__ uint32_t box_dstar_bound(const uint32_t* __restrict__ pyr, const DstarPyramid& D, int x0,
+                                                    int x1, int y0, int y1) {
+  int k = 0;
+  while (k + 1 < D.levels && ((x1 >> k) - (x0 >> k) > 1 || (y1 >> k) - (y0 >> k) > 1)) ++k;
+  const int w = D.w[k];
+  const uint32_t* L = pyr + D.off[k];
+  const int ax = x0 >> k, bx = x1 >> k, ay = y0 >> k, by = y1 >> k;
+  return max(max(__ldg(L + ay * w + ax), __ldg(L + ay * w + bx)), max(__ldg(L + by * w + ax), __ldg(L + by * w + bx)));
 }
 
 // The tiles of box row ty that the ellipse reaches: [tx_a, tx_b] (empty when

@@ -89,6 +89,33 @@ cudaError_t launch_dup_scan(int64_t n, uint32_t* counts, int64_t cap, int64_t* n
 // Key enumeration (duplicate.cu): which keys of the depth-ordered records'
 // support boxes are taken.
 enum { ENUM_ALL = 0, ENUM_KEPT = 1, ENUM_HELD = 2 };
+// Max pyramid of the per-tile proposal depth bits: level 0 is the tiles,
+// each next level the max over 2 x 2 cells of the one below (ceil halves), up
+// to one cell; levels are stored one after another in one array.
+constexpr int PYR_MAX = 24;
+struct DstarPyramid {
+  int levels;
+  int w[PYR_MAX], h[PYR_MAX];
+  int off[PYR_MAX];  // first word of each level
+};
+inline DstarPyramid make_dstar_pyramid(int tiles_x, int tiles_y) {
+  DstarPyramid d{};
+  int w = tiles_x, h = tiles_y, off = 0, k = 0;
+  for (;;) {
+    d.w[k] = w, d.h[k] = h, d.off[k] = off;
+    off += w * h;
+    ++k;
+    if ((w == 1 && h == 1) || k == PYR_MAX) break;
+    w = (w + 1) / 2, h = (h + 1) / 2;
+  }
+  d.levels = k;
+  return d;
+}
+inline int64_t dstar_pyramid_words(int tiles_x, int tiles_y) {
+  const DstarPyramid d = make_dstar_pyramid(tiles_x, tiles_y);
+  return (int64_t)d.off[d.levels - 1] + (int64_t)d.w[d.levels - 1] * d.h[d.levels - 1];
+}
+
 struct EnumArgs {
   int64_t R;                      // records in depth order
   const uint32_t* order;          // [R] record id at each depth rank
@@ -116,7 +143,8 @@ struct EnumArgs {
   uint32_t dmask[3];
   uint32_t* tile_hist;            // [key_passes][RADIX] digit counts (emit)
   unsigned long long* key_total;  // ENUM_KEPT count launch: all keys reached
-  uint8_t* has_held;              // ENUM_KEPT count launch: [tiles] set for tiles with keys beyond the proposal
+  const uint32_t* dstar_pyr;      // ENUM_KEPT: max pyramid of dstar_bits (level 0 is dstar_bits itself)
+  DstarPyramid pyr;
 };
 int64_t enum_warps(int64_t R);
 // 32-bit words of a warp-count buffer for R records: the counts, then the
@@ -176,8 +204,13 @@ cudaError_t launch_tile_hist_sorted(int64_t R, const uint32_t* order, const uint
                                     void* planes, cudaStream_t st);
 cudaError_t launch_features(void* planes, const CamDev& cam, const ParDev& P, void* x, int32_t* tile_total,
                             unsigned long long* key_total, cudaStream_t st);
-cudaError_t launch_dstar(int ntiles, const float* y, float margin, const float* dstar_in, uint32_t* bits,
-                         float* dstar_out, cudaStream_t st);
+// Proposal bits per tile (level 0 of the pyramid `pyr`, then its upper
+// levels) and has_held: whether any record of a depth bin that can lie beyond
+// the proposal has a support box covering the tile (from the prefixed
+// coverage planes, where every such record adds at least one unit): a
+// superset of the tiles with keys beyond their proposal.
+cudaError_t launch_dstar(const CamDev& cam, const float* y, float margin, const float* dstar_in, uint32_t* pyr,
+                         float* dstar_out, const void* planes, uint8_t* has_held, cudaStream_t st);
 // Summed-area table of the refuted flags, (tiles_x + 1) x (tiles_y + 1) ints.
 cudaError_t launch_refuted_sat(const uint8_t* refuted, const unsigned* n_refuted, int tiles_x, int tiles_y, int* sat,
                                cudaStream_t st);

@@ -33,7 +33,9 @@ namespace {
 constexpr int NBINS = 32;
 // Fixed-point unit of the coverage planes: unsigned 32-bit sums are exact
 // modulo 2^32 whatever the order of the atomics, and every prefix sum that is
-// read (one bin's coverage of a tile, far below 2^15) fits.
+// read (one bin's coverage of a tile, far below 2^15) fits.  Every record adds
+// at least one unit, so a tile's cell of a bin is nonzero exactly when a box
+// of that bin covers it.
 constexpr float MASS_ONE = 65536.f;
 
 __device__ __forceinline__ int depth_bin(float d, const DepthBins& B) {
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(int64_t R, const float4*
     const float box = (float)((tx1 - tx0 + 1) * (ty1 - ty0 + 1) * P.tile_w * P.tile_h);
     const float w = b.y * (1.f / 3.f) * fminf(1.f, ellipse / box);
     // fixed point: integer sums do not depend on the order of the atomics
-    const unsigned wq = (unsigned)__float2int_rn(w * MASS_ONE);
+    const unsigned wq = (unsigned)max(1, __float2int_rn(w * MASS_ONE));  // >= 1: a covered cell is never 0
     if (COUNTS != HIST_NONE) {
       atomicAdd(&cnt[ty0 * sx + tx0], 1);
       atomicAdd(&cnt[ty0 * sx + tx1 + 1], -1);
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(256) tile_hist_kernel(int64_t R, const float4*
 // at the end: shared-memory atomics per record, a few plane flushes per
 // block.  Same weights and fixed point as tile_hist_kernel, so the planes are
 // the same bit for bit.  Dynamic shared memory: one plane of unsigned cells.
-constexpr int HIST_SORTED_THREADS = 512;
+constexpr int HIST_SORTED_THREADS = 1024, HIST_SORTED_ITEMS = 4;
 
 __device__ __forceinline__ void flush_plane(unsigned* __restrict__ s_plane, unsigned* __restrict__ g_plane,
                                             int cells) {
@@ -121,6 +123,7 @@ __global__ void __launch_bounds__(HIST_SORTED_THREADS) tile_hist_sorted_kernel(
     int64_t R, const uint32_t* __restrict__ order, const uint32_t* __restrict__ dkey_sorted,
     const uint2* __restrict__ rect_sorted, const float4* __restrict__ rec, const CamDev cam, const ParDev P,
     const DepthBins bins, unsigned* __restrict__ mass) {
+  constexpr int CHUNK = HIST_SORTED_THREADS * HIST_SORTED_ITEMS;
   extern __shared__ unsigned s_plane[];
   __shared__ int s_bin[2];
   const int sx = cam.tiles_x + 1, cells = sx * (cam.tiles_y + 1);
@@ -128,32 +131,48 @@ __global__ void __launch_bounds__(HIST_SORTED_THREADS) tile_hist_sorted_kernel(
   const int64_t per = (R + gridDim.x - 1) / gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < R ? lo + per : R;
   int cur = -1;  // bin of the shared plane (block-uniform)
-  for (int64_t c0 = lo; c0 < hi; c0 += blockDim.x) {
-    const int64_t j = c0 + threadIdx.x;
-    int bin = -1;
-    unsigned wq = 0u;
-    uint2 rc = make_uint2(1u, 0u);
-    if (j < hi) {
-      const uint32_t dk = dkey_sorted[j];
-      rc = rect_sorted[j];
-      if (dk != DKEY_CULLED && (rc.x >> 16) >= (rc.x & 0xFFFFu)) {  // a non-empty box
-        const uint32_t r = order[j];
-        const float4 a = rec[3 * (size_t)r], b = rec[3 * (size_t)r + 1];  // {mx, my, l00, l01}, {l11, o, rho2, depth}
-        const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+  for (int64_t c0 = lo; c0 < hi; c0 += CHUNK) {
+    int bin[HIST_SORTED_ITEMS];
+    unsigned wq[HIST_SORTED_ITEMS];
+    uint2 rc[HIST_SORTED_ITEMS];
+    uint32_t r[HIST_SORTED_ITEMS];
+#pragma unroll
+    for (int i = 0; i < HIST_SORTED_ITEMS; ++i) {  // loads of all items first
+      const int64_t j = c0 + i * HIST_SORTED_THREADS + threadIdx.x;
+      bin[i] = -1;
+      rc[i] = make_uint2(1u, 0u);
+      r[i] = 0;
+      if (j < hi) {
+        const uint32_t dk = dkey_sorted[j];
+        rc[i] = rect_sorted[j];
+        if (dk != DKEY_CULLED && (rc[i].x >> 16) >= (rc[i].x & 0xFFFFu)) {  // a non-empty box
+          r[i] = order[j];
+          bin[i] = depth_bin(__uint_as_float(dk), bins);
+        }
+      }
+    }
+    int bmin = NBINS, bmax = -1;
+#pragma unroll
+    for (int i = 0; i < HIST_SORTED_ITEMS; ++i) {
+      wq[i] = 0u;
+      if (bin[i] >= 0) {
+        const float4 a = rec[3 * (size_t)r[i]], b = rec[3 * (size_t)r[i] + 1];  // {mx, my, l00, l01}, {l11, o, rho2, depth}
+        const int tx0 = rc[i].x & 0xFFFF, tx1 = rc[i].x >> 16, ty0 = rc[i].y & 0xFFFF, ty1 = rc[i].y >> 16;
         const float ellipse = 3.14159265f * b.z / fmaxf(a.z * b.x, 1e-30f);
         const float box = (float)((tx1 - tx0 + 1) * (ty1 - ty0 + 1) * P.tile_w * P.tile_h);
         const float w = b.y * (1.f / 3.f) * fminf(1.f, ellipse / box);
-        wq = (unsigned)__float2int_rn(w * MASS_ONE);
-        bin = depth_bin(__uint_as_float(dk), bins);
+        wq[i] = (unsigned)max(1, __float2int_rn(w * MASS_ONE));
+        bmin = min(bmin, bin[i]);
+        bmax = max(bmax, bin[i]);
       }
     }
     // bins rise with the depth order: the chunk's bins are [first, last] of
     // its binned records
     if (threadIdx.x == 0) s_bin[0] = NBINS, s_bin[1] = -1;
     __syncthreads();
-    if (bin >= 0) {
-      atomicMin(&s_bin[0], bin);
-      atomicMax(&s_bin[1], bin);
+    if (bmax >= 0) {
+      atomicMin(&s_bin[0], bmin);
+      atomicMax(&s_bin[1], bmax);
     }
     __syncthreads();
     const int b_first = s_bin[0], b_last = s_bin[1];
@@ -166,12 +185,15 @@ __global__ void __launch_bounds__(HIST_SORTED_THREADS) tile_hist_sorted_kernel(
         }
         cur = b;
       }
-      if (bin == b) {
-        const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
-        atomicAdd(&s_plane[ty0 * sx + tx0], wq);
-        atomicAdd(&s_plane[ty0 * sx + tx1 + 1], 0u - wq);
-        atomicAdd(&s_plane[(ty1 + 1) * sx + tx0], 0u - wq);
-        atomicAdd(&s_plane[(ty1 + 1) * sx + tx1 + 1], wq);
+#pragma unroll
+      for (int i = 0; i < HIST_SORTED_ITEMS; ++i) {
+        if (bin[i] == b) {
+          const int tx0 = rc[i].x & 0xFFFF, tx1 = rc[i].x >> 16, ty0 = rc[i].y & 0xFFFF, ty1 = rc[i].y >> 16;
+          atomicAdd(&s_plane[ty0 * sx + tx0], wq[i]);
+          atomicAdd(&s_plane[ty0 * sx + tx1 + 1], 0u - wq[i]);
+          atomicAdd(&s_plane[(ty1 + 1) * sx + tx0], 0u - wq[i]);
+          atomicAdd(&s_plane[(ty1 + 1) * sx + tx1 + 1], wq[i]);
+        }
       }
       __syncthreads();
     }
@@ -260,17 +282,47 @@ __global__ void __launch_bounds__(256) features_kernel(const unsigned* __restric
 }
 
 // Proposed depth per tile as comparable bits: exp(y + margin) from the MLP,
-// or the caller's depths (NaN or +inf keeps everything).
-__global__ void __launch_bounds__(256) dstar_kernel(int ntiles, const float* __restrict__ y, float margin,
+// or the caller's depths (NaN or +inf keeps everything); and has_held from the
+// prefixed coverage planes: records of bin b have depths below its upper
+// edge, so only bins whose upper edge exceeds the proposal can hold records
+// beyond it.
+__global__ void __launch_bounds__(256) dstar_kernel(const CamDev cam, const float* __restrict__ y, float margin,
                                                     const float* __restrict__ dstar_in, uint32_t* __restrict__ bits,
-                                                    float* __restrict__ dstar_out) {
+                                                    float* __restrict__ dstar_out, const unsigned* __restrict__ mass,
+                                                    const DepthBins B, uint8_t* __restrict__ has_held) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ntiles = cam.tiles_x * cam.tiles_y;
   if (t >= ntiles) return;
   float d = y ? expf(y[t] + margin) : dstar_in[t];
   if (!(d == d)) d = __int_as_float(0x7F800000);
   d = fmaxf(d, 0.f);
   bits[t] = __float_as_uint(d);
   if (dstar_out) dstar_out[t] = d;
+  const int tx = t % cam.tiles_x, ty = t / cam.tiles_x, sx = cam.tiles_x + 1;
+  const size_t plane = (size_t)sx * (cam.tiles_y + 1);
+  bool held = false;
+  for (int b = NBINS - 1; b >= 0 && !held; --b) {
+    const float upper = b < NBINS - 1 ? B.edge[b] : __int_as_float(0x7F800000);
+    if (!(upper > d)) break;  // this bin and all below end at or before the proposal
+    held = mass[(size_t)b * plane + ty * sx + tx] != 0u;
+  }
+  has_held[t] = held ? 1 : 0;
+}
+
+// Upper levels of the proposal pyramid (level 0 written by dstar_kernel).
+// One block.
+__global__ void __launch_bounds__(1024) dstar_pyramid_kernel(uint32_t* __restrict__ pyr, const DstarPyramid D) {
+  for (int k = 1; k < D.levels; ++k) {
+    const int w = D.w[k], h = D.h[k], pw = D.w[k - 1], ph = D.h[k - 1];
+    const uint32_t* lo = pyr + D.off[k - 1];
+    uint32_t* hi = pyr + D.off[k];
+    for (int i = threadIdx.x; i < w * h; i += blockDim.x) {
+      const int cx = i % w, cy = i / w, x0 = 2 * cx, y0 = 2 * cy;
+      const int x1 = min(x0 + 1, pw - 1), y1 = min(y0 + 1, ph - 1);
+      hi[i] = max(max(lo[y0 * pw + x0], lo[y0 * pw + x1]), max(lo[y1 * pw + x0], lo[y1 * pw + x1]));
+    }
+    __syncthreads();
+  }
 }
 
 // Summed-area table of the refuted flags over the tile grid, with a zero
@@ -352,8 +404,10 @@ cudaError_t launch_tile_hist_sorted(int64_t R, const uint32_t* order, const uint
   if (e == cudaSuccess && sm > 48 * 1024)
     e = cudaFuncSetAttribute(tile_hist_sorted_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  // two blocks per SM, each with at least a few chunks of records
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 2, ceil_div(R, 8 * HIST_SORTED_THREADS)));
+  // one block per SM: every block flushes each plane it touched once, so the
+  // global atomics grow with the number of blocks
+  const int64_t grid = std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)sms, ceil_div(R, 4 * HIST_SORTED_THREADS * HIST_SORTED_ITEMS)));
   tile_hist_sorted_kernel<<<(unsigned)grid, HIST_SORTED_THREADS, sm, st>>>(
       R, order, dkey_sorted, rect_sorted, rec, cam, P, make_depth_bins(), static_cast<unsigned*>(planes));
   return cudaGetLastError();
@@ -371,9 +425,14 @@ cudaError_t launch_features(void* planes, const CamDev& cam, const ParDev& P, vo
   return cudaGetLastError();
 }
 
-cudaError_t launch_dstar(int ntiles, const float* y, float margin, const float* dstar_in, uint32_t* bits,
-                         float* dstar_out, cudaStream_t st) {
-  dstar_kernel<<<ceil_div(ntiles, 256), 256, 0, st>>>(ntiles, y, margin, dstar_in, bits, dstar_out);
+cudaError_t launch_dstar(const CamDev& cam, const float* y, float margin, const float* dstar_in, uint32_t* pyr,
+                         float* dstar_out, const void* planes, uint8_t* has_held, cudaStream_t st) {
+  const int ntiles = cam.tiles_x * cam.tiles_y;
+  dstar_kernel<<<ceil_div(ntiles, 256), 256, 0, st>>>(cam, y, margin, dstar_in, pyr, dstar_out,
+                                                      static_cast<const unsigned*>(planes), make_depth_bins(),
+                                                      has_held);
+  const DstarPyramid D = make_dstar_pyramid(cam.tiles_x, cam.tiles_y);
+  if (D.levels > 1) dstar_pyramid_kernel<<<1, 1024, 0, st>>>(pyr, D);
   return cudaGetLastError();
 }
 

@@ -145,8 +145,10 @@ class LearnedRenderer:
         self._ws_ptr = (self._ws.data_ptr() + 255) // 256 * 256
         self._ws_bytes = wsb
 
-    def render(self, mlp: TerminationMLP | None = None, margin=0.0, dstar_in=None, t_thr=None):
-        """mlp, or per-tile depths dstar_in [tiles]; t_thr None = exact."""
+    def render(self, mlp: TerminationMLP | None = None, margin=0.0, dstar_in=None, t_thr=None, stats=True):
+        """mlp, or per-tile depths dstar_in [tiles]; t_thr None = exact;
+        stats=False leaves counters() as they were (and skips counting the
+        keys before truncation)."""
         sp = self.splats
         thr = self.params.t_min if t_thr is None else t_thr
         net = ctypes.byref(mlp.c()) if mlp is not None else None
@@ -155,7 +157,7 @@ class LearnedRenderer:
         N.check(N.lib().ls_render_learned(sp.n, _p(sp.means), _p(sp.scales), _p(sp.quats), _p(sp.opac), _p(sp.sh),
                                           ctypes.byref(self._c), ctypes.byref(self._pc), net, float(margin),
                                           _p(dstar_in), float(thr), self.capacity, _p(self.image), _p(self.T),
-                                          _p(self.n_last), _p(self.dstar), _p(self.stats),
+                                          _p(self.n_last), _p(self.dstar), _p(self.stats if stats else None),
                                           ctypes.c_void_p(self._ws_ptr), self._ws_bytes, _p(self.status), _stream()),
                 "ls_render_learned")
         return self.image, self.T

@@ -98,6 +98,13 @@ def test_learned_render_is_exact_for_any_proposal(margin):
     assert total == int(st0["n_keys"].item())
     if margin == -3.0:
         assert refuted > 0 and held > 0
+    # without the counters, records beyond their box's proposals are dropped
+    # up front: the same image
+    img, T = lr.render(net, margin=margin, stats=False)
+    torch.cuda.synchronize()
+    lr.check()
+    assert torch.equal(img, img0) and torch.equal(T, T0)
+    assert torch.equal(lr.n_last, st0["n_last"])
 
 
 def test_learned_proposals_follow_the_tile_features():
