@@ -388,6 +388,34 @@ def bench_learned(dev, reps=20):
     return out
 
 
+def learned_probe():
+    """One plain forward frame, then one learned frame (trained network,
+    calibrated margin, no counters) of the 5M 1080p workload, after one
+    untimed frame of each: the launch list of a profiler run shows both."""
+    import torch
+    from paper_2411_12440_gb300 import raster, scenes
+    from paper_2411_12440_gb300.learned import LearnedRenderer, TerminationMLP
+    dev = torch.device("cuda", 0)
+    net = TerminationMLP.load(os.path.join(ROOT, "paper_2411_12440_gb300", "data", "termination_mlp.npz"),
+                              device=dev)
+    margin, t_thr = float(net.meta["margin"]), float(net.meta["t_thr"])
+    scene, cams, _ = scenes.make_workload("learned_5m_1080p")
+    cam = cams[0]
+    sp = raster.Splats.from_scene(scene, device=dev)
+    del scene
+    P = raster.RenderParams(sh_degree=3)
+    rz = raster.Rasterizer(P, device=dev)
+    lr = LearnedRenderer(sp, cam, P, device=dev)
+    rz.forward(sp, cam)  # capacity from an exact count
+    for _ in range(2):
+        rz.forward(sp, cam, sync_capacity=False)
+        lr.render(mlp=net, margin=margin, t_thr=t_thr, stats=False)
+    torch.cuda.synchronize(dev)
+    rz.check_status("plain")
+    lr.check()
+    print(json.dumps({"learned_probe": "learned_5m_1080p", "frames": ["plain", "mlp", "plain", "mlp"]}))
+
+
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
@@ -404,9 +432,13 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-camera batched measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-termination measurement")
     ap.add_argument("--no-family", action="store_true", help="skip the linear-vs-Gaussian measurement")
+    ap.add_argument("--learned-probe", action="store_true",
+                    help="one plain and one learned forward frame of the 5M 1080p workload (for a launch list)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.learned_probe:
+        return learned_probe()
     args.warmup = max(args.warmup, 3)
 
     import numpy as np

@@ -357,6 +357,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
   if (my_max > 0) atomicMax(s_max, my_max);
   __syncthreads();
   const int max_last = *s_max;
+  const int warp_max = __reduce_max_sync(FULL, my_max);  // entries at or past it touch none of the warp's pixels
 
   for (int b_end = max_last; b_end > 0; b_end -= B) {
     const int b0 = max(0, b_end - B);
@@ -373,7 +374,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
       for (int m = 0; m < 9; ++m) s_acc[9 * k + m] = 0.f;
     }
     __syncthreads();
-    for (int jj = cnt - 1; jj >= 0; --jj) {
+    for (int jj = min(cnt, warp_max - b0) - 1; jj >= 0; --jj) {
       const int j = b0 + jj;
       const float4 a = s_a[jj];
       const float4 bb = s_b[jj];
@@ -381,12 +382,15 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
       const float l01dy = __fmul_rn(a.w, dy);
       const float e2 = __fmul_rn(bb.x, dy);
       const float e2s = __fmul_rn(e2, e2);
+      // else q >= e2s > rho^2 for the whole row, or every pixel of the
+      // thread composited its last entry in front of this one
+      const bool row_in = e2s <= bb.z && j < my_max;
+      if (!__any_sync(FULL, row_in)) continue;  // nothing for the warp
       // per-thread sums: the geometric terms are gathered as sums over the
       // thread's pixels of gq e1, gq dx, gq dx^2 and gq (dy and l11 dy are the
       // same for its whole row) and expanded once per record below
       float s_e1 = 0.f, s_dx = 0.f, s_dx2 = 0.f, s_q = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
       bool any = false;
-      const bool row_in = e2s <= bb.z;  // else q >= e2s > rho^2 for the whole row
       const float kq = 0.5f * bb.y * P.inv_lambda;
 #pragma unroll
       for (int p = 0; p < PPT; ++p) {
@@ -413,7 +417,8 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
         if (araw <= P.alpha_max) {
           v5 += f * ga;
           // dL/dq = dL/dalpha o f'(x) / (lambda 2 D), o / (2 lambda) per record
-          float gD = ga * kern_df<KID>(xk) * kq;
+          // (the linear profile's slope is -1 wherever alpha > 0)
+          float gD = (KID == LS_KERNEL_LINEAR ? -ga : ga * kern_df<KID>(xk)) * kq;
           if (P.ags == 1) gD *= __expf(-D * D);
           else if (P.ags == 2) gD *= __expf(-xk * xk);
           const float gq = D > 0.f ? __fdividef(gD, D) : 0.f;
