@@ -244,7 +244,10 @@ __global__ void __launch_bounds__(128) blend_fwd_kernel(const float4* __restrict
                                                         float* __restrict__ t_final, int32_t* __restrict__ n_last,
                                                         unsigned long long* stats, const TruncArgs ta) {
   extern __shared__ float4 smem[];
-  const int B = 4 * blockDim.x;
+  // two records per thread per batch: tiles of dense scenes stop within a
+  // few hundred entries, and a smaller batch gathers fewer records that no
+  // pixel reads (measured 5 % faster than four per thread)
+  const int B = 2 * blockDim.x;
   const int tile = blockIdx.x;
   TileJob J;
   J.x0 = (tile % cam.tiles_x) * P.tile_w;
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(128) blend_trunc_kernel(const float4* __restri
                                                           float* __restrict__ t_final, int32_t* __restrict__ n_last,
                                                           const TruncArgs ta) {
   extern __shared__ float4 smem[];
-  const int B = 4 * blockDim.x;
+  const int B = 2 * blockDim.x;
   const int tile = blockIdx.x;
   if (MODE == FWD_RESUME && !ta.refuted[tile]) return;
   TileJob J;
@@ -582,7 +585,7 @@ cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev&
   const int ppt = ppt_for(P);
   const int threads = P.tile_w * P.tile_h / ppt;
   const unsigned grid = (unsigned)(cam.tiles_x * cam.tiles_y);
-  const size_t sm = sizeof(float4) * 3 * 4 * threads;
+  const size_t sm = sizeof(float4) * 3 * 2 * threads;
 #define LS_BF3(K, PP, C)                                                                                   \
   blend_fwd_kernel<K, PP, C><<<grid, threads, sm, st>>>(rec, cam, P, ranges, vals, image, t_final, n_last, stats, \
                                                         labels_ta)
@@ -647,7 +650,7 @@ cudaError_t launch_blend_trunc(int mode, const float4* rec, const CamDev& cam, c
   const int ppt = ppt_for(P);
   const int threads = P.tile_w * P.tile_h / ppt;
   const unsigned grid = (unsigned)(cam.tiles_x * cam.tiles_y);
-  const size_t sm = sizeof(float4) * 3 * 4 * threads;
+  const size_t sm = sizeof(float4) * 3 * 2 * threads;
 #define LS_BT3(K, PP, M) \
   blend_trunc_kernel<K, PP, M><<<grid, threads, sm, st>>>(rec, cam, P, ranges, vals, image, t_final, n_last, ta)
 #define LS_BT2(K, PP)                        \
