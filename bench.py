@@ -34,8 +34,9 @@ SM_MAX_MHZ = 2070.0
 LANES_PER_SM = 128
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture
-# (profiles/), valid only while the kernel source is the one measured.
-NCU_TRAFFIC = {}
+# (profiles/blend_bwd_3m_1080p.md: dram__bytes_read.sum + dram__bytes_write.sum),
+# valid only while the kernel source is the one measured.
+NCU_TRAFFIC = {"blend_bwd": {"bytes": 71513088 + 1459200, "src": "c481e18152e4"}}
 
 
 def _src_hash(name):
@@ -239,23 +240,31 @@ def bench_batched(dev, reps=10):
     K = int(br.n_keys.item())
     del br
     torch.cuda.empty_cache()
-    # the plain path, one camera at a time, same tile shape
-    rz = raster.Rasterizer(dataclasses.replace(Pt), device=dev)
-    for cam in cams:
-        rz.forward(sp, cam, sync_capacity=True)
-    torch.cuda.synchronize(dev)
-    e0.record()
-    for cam in cams:
-        rz.forward(sp, cam, sync_capacity=False)
-    e1.record()
-    torch.cuda.synchronize(dev)
-    rz.check_status("plain cameras")
-    ms_plain = e0.elapsed_time(e1)
+    # the plain path, one camera at a time, at the faster of the tuned tile
+    # shape and its default 16x16
+    plain_ms = {}
+    for tile in dict.fromkeys([tuple(tune.tile), (16, 16)]):
+        rz = raster.Rasterizer(dataclasses.replace(P, tile_w=tile[0], tile_h=tile[1]), device=dev)
+        for cam in cams:
+            rz.forward(sp, cam, sync_capacity=True)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for cam in cams:
+            rz.forward(sp, cam, sync_capacity=False)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        rz.check_status("plain cameras")
+        plain_ms["%dx%d" % tile] = e0.elapsed_time(e1)
+        del rz
+        torch.cuda.empty_cache()
+    plain_tile = min(plain_ms, key=plain_ms.get)
+    ms_plain = plain_ms[plain_tile]
     pixels = sum(c["width"] * c["height"] for c in cams)
     return {"workload": "batch_3m_64cams", "cams": len(cams), "prims": scene.n, "pixels": pixels, "tile_keys": K,
             "tile": "%dx%d" % tune.tile, "blend_batch": tune.blend_batch, "graph": True,
             "ms_per_batch": ms_batch, "frames_per_s": len(cams) * 1e3 / ms_batch,
             "plain_ms_per_batch": ms_plain, "plain_frames_per_s": len(cams) * 1e3 / ms_plain,
+            "plain_tile": plain_tile, "plain_ms_by_tile": {k: round(v, 3) for k, v in plain_ms.items()},
             "speedup_vs_plain": ms_plain / ms_batch,
             "autotune_ms": {"%dx%d/b%d" % k: round(v, 3) for k, v in tune.table.items()}}
 
@@ -462,7 +471,9 @@ def main():
     gout = dict(means=torch.empty_like(sp.means), scales=torch.empty_like(sp.scales),
                 quats=torch.empty_like(sp.quats), opac=torch.empty_like(sp.opac), sh=torch.empty_like(sp.sh))
 
-    stage_names = ["project", "duplicate_sort", "blend_fwd", "blend_bwd", "project_bwd"]
+    # g2d_clear (the zeroed gradient buffer the backward accumulates into) is
+    # timed apart so that blend_bwd brackets that one kernel
+    stage_names = ["project", "duplicate_sort", "blend_fwd", "g2d_clear", "blend_bwd", "project_bwd"]
 
     def step(evs=None, bwd=True, splats=None, grad_image=None, grad_t=None, outg=None):
         spx = splats or sp
@@ -477,11 +488,12 @@ def main():
         if not bwd:
             return image, T, None
         g2d.zero_()
+        rec(4)
         rz.blend_bwd(proj, R, cam, ranges, vals, T, n_last, grad_image if grad_image is not None else gimg,
                      grad_t if grad_t is not None else gT, g2d)
-        rec(4)
-        g = rz.project_bwd(spx, [cam], proj, g2d, out=outg or gout)
         rec(5)
+        g = rz.project_bwd(spx, [cam], proj, g2d, out=outg or gout)
+        rec(6)
         return image, T, g
 
     # capacity from an exact count, then no host syncs inside steps
@@ -500,7 +512,7 @@ def main():
     rz.check_status("warmup")
 
     # ---------------------------------------------------------------- timed fwd+bwd
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stage_names) + 1)] for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     barrier(ws)
@@ -640,18 +652,27 @@ def main():
         "blend_bwd": ("alu", 7 * n_eval + 40 * n_contrib),
         # params + SH3 and g2d read, 236 B of gradients written
         "project_bwd": ("hbm", (236 + 48 + 4 + 236) * R),
+        # 48 B per record zeroed
+        "g2d_clear": ("hbm", 48 * R),
     }
-    dom = max(stage_ms, key=lambda k: stage_ms[k])
-    bound, amount = units[dom]
-    sec = stage_ms[dom] * 1e-3
-    if bound == "hbm":
-        achieved = amount / sec / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": peak_src}
-    else:
+
+    def roofline_of(stage):
+        bound, amount = units[stage]
+        sec = stage_ms[stage] * 1e-3
+        if bound == "hbm":
+            achieved = amount / sec / 1e9
+            return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "peak_source": peak_src}
         achieved = amount / sec / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz"}
+        return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz"}
+
+    # the dominant kernel: the longest stage that is one launch (duplicate_sort
+    # is a chain of a dozen launches, none of them longer than the blends)
+    dom = max((k for k in stage_ms if k not in ("duplicate_sort", "g2d_clear")), key=lambda k: stage_ms[k])
+    roof = roofline_of(dom)
+    stage_roofs = {k: {"bound": r["bound"], "achieved": round(r["achieved"], 3), "unit": r["unit"],
+                       "frac": round(r["frac"], 4)} for k, r in ((k, roofline_of(k)) for k in stage_ms)}
     tr = NCU_TRAFFIC.get(dom)
     src = {"blend_fwd": "blend.cu", "blend_bwd": "blend.cu", "project": "project.cu", "project_bwd": "project.cu",
            "duplicate_sort": "sort.cu"}[dom]
@@ -667,6 +688,7 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single"},
             "fwd_fps": ws * 1e3 / fwd_ms, "fwd_ms": fwd_ms,
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "stage_rooflines": stage_roofs,
             "units": {"tile_keys": K, "box_tile_keys": K_box, "visible": n_vis, "pairs_evaluated": n_eval,
                       "pairs_composited": n_contrib},
             "roofline": roof, "clocks": clocks.summary(), "e2e": e2e,
