@@ -521,6 +521,7 @@ struct LearnedWs {
   int* sat;
   int64_t *n_kept, *n_kept_valid, *n_held, *n_held_valid;
   unsigned* n_refuted;
+  unsigned* refuted_floor;
   unsigned long long* key_total;
   size_t zero_begin, zero_bytes;
   char *depth_scratch, *kept_scratch, *held_scratch;
@@ -572,6 +573,7 @@ LearnedWs learned_layout(char* base, int64_t R, int64_t cap, int tiles_x, int ti
   w.n_held = reinterpret_cast<int64_t*>(take(8));
   w.n_held_valid = reinterpret_cast<int64_t*>(take(8));
   w.n_refuted = reinterpret_cast<unsigned*>(take(4));
+  w.refuted_floor = reinterpret_cast<unsigned*>(take(4));
   w.key_total = reinterpret_cast<unsigned long long*>(take(8));
   w.depth_scratch = take(sort_scratch_bytes((int64_t)Rz, 4));
   w.kept_scratch = take(sort_scratch_bytes((int64_t)Cz, kp));
@@ -700,6 +702,7 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   ea.refuted = w.refuted;
   ea.sat = w.sat;
   ea.n_refuted = w.n_refuted;
+  ea.refuted_floor = w.refuted_floor;
   ea.key_passes = kp;
   for (int p = 0; p < kp; ++p) {
     ea.dshift[p] = td.shift[p];
@@ -733,6 +736,8 @@ ls_status ls_render_learned(int32_t n, const float* means, const float* scales, 
   ta.has_held = w.has_held;
   ta.refuted = w.refuted;
   ta.n_refuted = w.n_refuted;
+  ta.dstar_bits = w.dstar_bits;
+  ta.refuted_floor = w.refuted_floor;
   ta.kept_ranges = reinterpret_cast<const int2*>(w.k_ranges);
   LS_TRY(launch_blend_trunc(1, pp.rec, C, P, reinterpret_cast<const int2*>(w.k_ranges), w.k_vals, image, t_final,
                             n_last, ta, st));

@@ -174,6 +174,7 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
     if (raw && threadIdx.x == 0) {
       ta.refuted[tile_gid] = 1;
       atomicAdd(ta.n_refuted, 1u);
+      atomicMax(ta.refuted_floor, ~ta.dstar_bits[tile_gid]);
     }
   }
 #pragma unroll

@@ -201,7 +201,15 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t gw = (int64_t)blockIdx.x * ENUM_WARPS + warp;
-  if ((MODE == ENUM_HELD && *A.n_refuted == 0u) || (EMIT && *A.n_valid == 0)) {
+  // ENUM_HELD: a record at or in front of the smallest proposal of a refuted
+  // tile has no held-out key; depth order puts all such records first
+  const uint32_t held_lim = MODE == ENUM_HELD ? ~*A.refuted_floor : 0u;
+  bool none_here = false;
+  if (MODE == ENUM_HELD) {
+    const int64_t jl = min(A.R, (int64_t)(blockIdx.x + 1) * ENUM_BLOCK_RECS) - 1;
+    none_here = A.dkey_sorted[jl] <= held_lim;
+  }
+  if ((MODE == ENUM_HELD && (*A.n_refuted == 0u || none_here)) || (EMIT && *A.n_valid == 0)) {
     if (!EMIT && lane == 0) {
       A.warp_counts[gw] = 0u;
       A.warp_tbase[gw] = NO_STASH;
@@ -268,6 +276,7 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
         r = A.order[j];
         if (MODE != ENUM_ALL) dk = A.dkey_sorted[j];
       }
+      if (MODE == ENUM_HELD && dk <= held_lim) rc = make_uint2(1u, 0u);
       if (MODE == ENUM_HELD && box_rows(rc)) {
         const int x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF, y1 = rc.y >> 16;
         const int* sat = A.sat;

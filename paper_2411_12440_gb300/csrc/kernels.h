@@ -129,6 +129,7 @@ struct EnumArgs {
   const uint8_t* refuted;         // [tiles] (ENUM_HELD)
   const int* sat;                 // summed-area table of refuted (ENUM_HELD)
   const unsigned* n_refuted;      // (ENUM_HELD)
+  const unsigned* refuted_floor;  // (ENUM_HELD) ~(smallest proposal bits of a refuted tile)
   uint32_t* warp_counts;          // [n_warps] taken keys per warp, then scanned offsets
   uint32_t* warp_tbase;           // [n_warps] stash offset of each warp's keys (0xFFFFFFFF: none)
   int64_t n_warps;                // enum_warps(R)
@@ -168,6 +169,8 @@ struct TruncArgs {
   const uint8_t* has_held;    // [tiles] set when the tile has keys beyond its proposal
   uint8_t* refuted;           // [tiles] set for refuted tiles
   unsigned* n_refuted;
+  const uint32_t* dstar_bits;  // [tiles] proposal bits
+  unsigned* refuted_floor;     // ~(smallest proposal bits of a refuted tile); zero before the pass
   const int2* kept_ranges;    // resume: the kept list of each tile
   float* labels;              // counting forward: per-tile termination depth
 };
