@@ -582,8 +582,8 @@ def main():
                         df, hf = d.view(-1), h.view(-1)
                         n = df.numel()
                         lo, hi = n * j // len(streams), n * (j + 1) // len(streams)
-                        if hi > lo:
-                            df[lo:hi].copy_(hf[lo:hi], non_blocking=True)
+                        if hi > lo:  # through the library's host-link copy (ls_copy)
+                            raster.copy_(df[lo:hi], hf[lo:hi], st_)
                     ev = torch.cuda.Event()
                     ev.record(st_)
                     evs.append(ev)

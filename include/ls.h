@@ -323,6 +323,14 @@ ls_status ls_duplicate_sort_noalloc(int64_t n_records, const void* proj, const l
                                     const ls_params* params, int64_t key_capacity, uint32_t* keys, uint32_t* vals,
                                     int64_t* n_keys_dev, int32_t* tile_ranges, int32_t* status_dev, void* stream);
 
+/* Copy of `bytes` bytes from src to dst where each side is device memory or
+ * host memory pinned through the CUDA runtime (cudaHostAlloc /
+ * cudaHostRegister), in either direction, on the copy engines.  For the
+ * host<->device moves of an end-to-end step.  LS_ERR_INVALID_ARG when a
+ * pointer is NULL or not device-addressable (pageable host memory): nothing
+ * is enqueued. */
+ls_status ls_copy(void* dst, const void* src, size_t bytes, void* stream);
+
 /* Text of a status code (static storage). */
 const char* ls_status_string(int32_t status);
 

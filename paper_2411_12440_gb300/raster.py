@@ -128,6 +128,19 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def copy_(dst, src, stream=None):
+    """dst <- src (same size, contiguous) between device memory and pinned
+    host memory, either way, enqueued on `stream` (default: the current one)."""
+    if not (dst.is_contiguous() and src.is_contiguous()):
+        raise ValueError("contiguous tensors")
+    n = dst.numel() * dst.element_size()
+    if n != src.numel() * src.element_size():
+        raise ValueError("sizes differ")
+    st = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    N.check(N.lib().ls_copy(_p(dst), _p(src), n, st), "ls_copy")
+    return dst
+
+
 def _dev_check(t, name):
     if not t.is_cuda:
         raise ValueError("%s must be a CUDA tensor" % name)
