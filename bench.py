@@ -44,6 +44,25 @@ def _src_hash(name):
     return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
 
 
+def measure_fp32_issue(dev, iters=200_000):
+    """Dependent-free FP32 FMA lane instructions per second (T), from the
+    library's probe timed with CUDA events after one warm-up launch."""
+    import ctypes
+    import torch
+    from paper_2411_12440_gb300 import _native as N
+    out = torch.zeros(1, dtype=torch.float32, device=dev)
+    ops = ctypes.c_int64(0)
+    st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    L = N.lib()
+    N.check(L.ls_fp32_issue_probe(iters // 10, 8, ctypes.c_void_p(out.data_ptr()), ctypes.byref(ops), st), "probe")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    N.check(L.ls_fp32_issue_probe(iters, 8, ctypes.c_void_p(out.data_ptr()), ctypes.byref(ops), st), "probe")
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return ops.value / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -636,6 +655,7 @@ def main():
     # ---------------------------------------------------------------- roofline of the dominant kernel
     hbm_peak, peak_src = _peaks()
     alu_peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12  # Tops/s, FP32 lane instructions
+    fma_probe = measure_fp32_issue(dev)  # the same rate measured with the library's dependent-free FMA probe
     kp = 2
     nt = raster.tiles_of(cam, P)
     units = {
@@ -671,6 +691,8 @@ def main():
     # is a chain of a dozen launches, none of them longer than the blends)
     dom = max((k for k in stage_ms if k not in ("duplicate_sort", "g2d_clear")), key=lambda k: stage_ms[k])
     roof = roofline_of(dom)
+    if roof["bound"] == "alu":
+        roof["peak_check"] = {"measured_fma_tops": round(fma_probe, 3), "of_peak": round(fma_probe / alu_peak, 4)}
     stage_roofs = {k: {"bound": r["bound"], "achieved": round(r["achieved"], 3), "unit": r["unit"],
                        "frac": round(r["frac"], 4)} for k, r in ((k, roofline_of(k)) for k in stage_ms)}
     tr = NCU_TRAFFIC.get(dom)
@@ -694,7 +716,9 @@ def main():
             "roofline": roof, "clocks": clocks.summary(), "e2e": e2e,
             # per step: project 1; duplicate_sort 12 + kp (depth histogram, scan, 4 passes, boxes, key count,
             # scan, key copy, digit scan, kp tile passes, ranges); blend fwd, blend bwd, project bwd 1 each
-            "gpu_launches": args.steps * (1 + (12 + kp) + 3)}
+            # per step: project; histogram, scan, 4 depth passes, boxes, key count, 2-launch warp-count
+            # scan, key copy, digit scan, kp tile passes, ranges; blend_fwd, blend_bwd, project_bwd
+            "gpu_launches": args.steps * (1 + (13 + kp) + 3)}
 
     if not args.no_batch and args.prims is None:
         line["batched"] = bench_batched(dev)

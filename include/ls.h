@@ -331,6 +331,14 @@ ls_status ls_duplicate_sort_noalloc(int64_t n_records, const void* proj, const l
  * is enqueued. */
 ls_status ls_copy(void* dst, const void* src, size_t bytes, void* stream);
 
+/* Throughput probe of dependent-free FP32 FMAs (the denominator of the
+ * blending rooflines, checked by measurement): blocks_per_sm x SMs blocks of
+ * 256 threads, each running `iters` rounds of eight independent FMA chains.
+ * *lane_ops (host) receives the FP32 lane instructions the launch executes;
+ * time it with events on `stream`.  out: one float of device memory (written
+ * only to keep the chains live). */
+ls_status ls_fp32_issue_probe(int64_t iters, int32_t blocks_per_sm, float* out, int64_t* lane_ops, void* stream);
+
 /* Text of a status code (static storage). */
 const char* ls_status_string(int32_t status);
 

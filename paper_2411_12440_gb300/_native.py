@@ -75,6 +75,7 @@ PROTOTYPES = {
     "ls_render_bwd": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                              _P, _P, _P, _SZ, _P, _P]),
     "ls_copy": (_I32, [_P, _P, _SZ, _P]),
+    "ls_fp32_issue_probe": (_I32, [_I64, _I32, _P, ctypes.POINTER(ctypes.c_int64), _P]),
 }
 
 _lib = None
