@@ -19,9 +19,11 @@ cudaError_t launch_project_bwd(int n, const float* means, const float* scales, c
 
 // ---- onesweep radix sort (sort.cu)
 constexpr int SORT_THREADS = 256;
-// Keys per thread of a partition (3840-key partitions; 8, 11, 19 and 24
-// measured slower on the bench frame, for the depth sort as well).
-constexpr int SORT_ITEMS = 15;
+// Keys per thread of a partition: 4608-key partitions take 55 KB of shared
+// memory, so four CTAs still fit an SM.  On the bench frame 8, 11, 13, 15, 16
+// and 17 were slower (more partitions to look back over), 19 and 24 too
+// (three CTAs per SM).
+constexpr int SORT_ITEMS = 18;
 constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per partition
 constexpr int RADIX = 256;
 
