@@ -6,9 +6,11 @@
 // apart, so one shared-memory read of a record serves PPT pixels and the
 // per-record terms that depend only on the row (dy, l01 dy, l11 dy) are
 // computed once.  A warp's p-th pixels then form a compact block (8 x 4 for
-// 16 x 16 tiles), so the per-pixel work, which runs once per p for the lanes
-// whose p-th pixel takes the record, wastes fewer lanes than with contiguous
-// strips (whose p-th pixels are 4 columns apart).
+// 16 x 16 tiles at 4 pixels per thread, 4 x 8 at 2), so the per-pixel work,
+// which runs once per p for the lanes whose p-th pixel takes the record,
+// wastes fewer lanes than with contiguous strips (whose p-th pixels are PPT
+// columns apart).  The forward runs 2 pixels per thread on 16 x 16 tiles, the
+// backward 4.
 // The tile's sorted record ids are walked in batches: the threads gather the
 // batch's 48-byte records into shared memory (each record is fetched from
 // L2/HBM once per tile), then every thread reads them as broadcasts.
@@ -583,7 +585,9 @@ cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev&
                              unsigned long long* stats, cudaStream_t st, float* labels) {
   TruncArgs labels_ta{};
   labels_ta.labels = labels;
-  const int ppt = ppt_for(P);
+  // the forward runs 2 pixels per thread up to 16x16 tiles (128 threads; 2 %
+  // faster than 4 there), the backward keeps 4
+  const int ppt = P.tile_w * P.tile_h <= 256 ? 2 : 4;
   const int threads = P.tile_w * P.tile_h / ppt;
   const unsigned grid = (unsigned)(cam.tiles_x * cam.tiles_y);
   const size_t sm = sizeof(float4) * 3 * 2 * threads;

@@ -78,8 +78,6 @@ cudaError_t launch_ranges_fixup(int32_t* ranges, int total_tiles, cudaStream_t s
 
 // ---- duplication and tile ranges (duplicate.cu)
 constexpr int DUP_THREADS = 256;
-constexpr int DUP_ITEMS = 2;
-constexpr int DUP_BLOCK = DUP_THREADS * DUP_ITEMS;
 cudaError_t launch_dup_count(int64_t R, const uint32_t* order, const uint32_t* dkey_sorted, const float4* foot,
                              const CamTable& cams, int n_per_cam, const ParDev& P, uint2* rect_sorted, cudaStream_t st);
 // Exclusive scan of n = enum_warps(R) counts in place (the buffer holds
