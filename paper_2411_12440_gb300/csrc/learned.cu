@@ -4,17 +4,22 @@
 //                coverage of the records whose support box covers it, and
 //                their number, as 2D difference arrays (four atomics per
 //                record and plane, not one per (record, tile) key) followed by
-//                2D prefix sums;
+//                2D prefix sums; tile_hist_sorted builds the same coverage
+//                planes from the depth order, one bin's plane at a time in
+//                shared memory (the learned render's path);
 //   features     log1p of the cumulative coverage in front of each bin edge
 //                and the world direction of the tile's centre ray: the MLP's
 //                35 inputs (fp16 rows of 48);
 //   dstar        the proposed depth per tile, exp(MLP output + margin), as
-//                comparable binary32 bits;
+//                comparable binary32 bits, whether a tile may hold keys beyond
+//                its proposal (has_held, from the coverage planes), and a max
+//                pyramid of the proposals that bounds them over any support box
+//                (the kept enumeration drops records beyond that bound);
 //   refuted_sat  summed-area table of the refuted tiles, so that the
 //                held-out enumeration (duplicate.cu, ENUM_HELD) skips records
 //                whose box holds none;
 //   orchestration of ls_render_learned: kept keys are sorted and blended; a
-//   tile whose pixels did not all settle and that has held-out keys is
+//   tile whose pixels did not all settle and that may hold held-out keys is
 //   refuted, its held-out keys are sorted and blending resumes from the stored
 //   per-pixel state, so the image is the plain one bit for bit (t_thr =
 //   t_min) or within t_thr (max rgb + bg) of it (t_thr > t_min).
