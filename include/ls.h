@@ -255,8 +255,10 @@ ls_status ls_tile_features(const void* proj, int64_t n_records, const ls_camera*
  * when mlp is NULL, the caller's per-tile depths dstar_in [tiles]) proposes
  * per tile a depth d* = exp(MLP + margin); only keys with depth <= d* are
  * sorted and blended.  A tile is final when every pixel stopped or has
- * T < t_thr, or when it has no held-out keys; otherwise it is refuted and
- * blending resumes over its held-out keys from the stored per-pixel state.
+ * T < t_thr, or when no record of a depth bin reaching beyond d* has a
+ * support box covering it (so it has no held-out keys); otherwise it is
+ * refuted and blending resumes over its held-out keys (possibly none) from
+ * the stored per-pixel state.
  * With t_thr <= params->t_min the image equals ls_render_fwd's bit for bit;
  * with a larger t_thr each pixel is within t_thr (max rgb + bg) of it.
  * Outputs as ls_render_fwd (n_last continues into the held-out lists),
