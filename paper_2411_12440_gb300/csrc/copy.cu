@@ -12,7 +12,7 @@
 namespace {
 
 // Device-addressable: device or managed memory, or host memory pinned
-// through the CUDA runtime (registered with the driver).
+// through the CUDA runtime (page-locked and mapped for the device).
 bool device_addressable(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
