@@ -207,8 +207,8 @@ def run_reference(args):
     scene, cams, extra = scenes.make_workload(WORKLOAD)
     P = dict(sh_degree=3, antialias=int(extra["antialias"]))
     # each step is the bounded sample of the cpu_baseline leg (~6 s of host
-    # work); at most 3 timed steps after at most 1 warm-up keep the run short
-    steps, warmup = min(args.steps, 3), min(args.warmup, 1)
+    # work); at most 3 warm-up and 3 timed steps keep the run near a minute
+    steps, warmup = min(args.steps, 3), min(args.warmup, 3)
     ests = []
     sample = ""
     for i in range(warmup + steps):
