@@ -119,15 +119,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(args):
+def dist_setup(args, backend="nccl"):
+    """Rank layout from the torchrun environment; one process group over all
+    ranks when there is more than one (nccl on the GPUs; gloo in CPU tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -137,14 +142,21 @@ def barrier(ws):
         dist.barrier()
 
 
-def max_over_ranks(x, ws):
+def max_over_ranks(x, ws, device="cuda"):
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(ws, ms_per_step):
+    """Whole-job steps per second: every rank runs its own replica of the
+    frame (weak scaling), so N ranks finish N frames per slowest step."""
+    return ws * 1e3 / ms_per_step
 
 
 # --------------------------------------------------------------------------
@@ -646,11 +658,11 @@ def main():
         barrier(ws)
         e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws) / n_e2e
         rz.check_status("e2e")
-        e2e = {"value": ws * 1e3 / e2e_ms, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        e2e = {"value": job_rate(ws, e2e_ms), "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "overlap": "uploads, compute and read-backs on three streams, double-buffered"}
 
     ms = total_ms / args.steps
-    value = ws * 1e3 / ms
+    value = job_rate(ws, ms)
 
     # ---------------------------------------------------------------- roofline of the dominant kernel
     hbm_peak, peak_src = _peaks()
@@ -708,7 +720,7 @@ def main():
                    "width": W, "height": H, "sh_degree": 3,
                        "tile": "%dx%d" % (P.tile_w, P.tile_h), "l2": "inputs larger than L2 (708 MB of parameters)",
                        "parallelism": "replicas" if ws > 1 else "single"},
-            "fwd_fps": ws * 1e3 / fwd_ms, "fwd_ms": fwd_ms,
+            "fwd_fps": job_rate(ws, fwd_ms), "fwd_ms": fwd_ms,
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "stage_rooflines": stage_roofs,
             "units": {"tile_keys": K, "box_tile_keys": K_box, "visible": n_vis, "pairs_evaluated": n_eval,
