@@ -8,7 +8,9 @@ Functions follow the paper's definitions (Sec. 3.1 Eq. 1-6, Sec. 3.2 Eq. 7-11,
 Sec. 3.3 Eq. 12-14, Appendix B Eq. 19-26); the readings where the paper is
 silent are listed at the top of lso.cpp.  Parity is pinned by tests in
 tests/test_oracle_*.py (closed forms, brute force, invariants, finite
-differences); the anti-aliasing compensation constants are parity unpinned.
+differences), the anti-aliasing opacity compensation included (its value at
+eps2d = 0, closed forms for isotropic and rotated anisotropic footprints, and
+the footprint integral it preserves).
 """
 from __future__ import annotations
 

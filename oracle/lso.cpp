@@ -26,8 +26,10 @@
 // alpha_max, alpha skip below alpha_min, stop when T would fall below T_min
 // (that entry excluded), ties in depth broken by primitive id, real SH basis
 // with the Condon-Shortley phase (3DGS sign table), colour = SH + 0.5 clamped
-// at 0.  Only the anti-aliasing compensation constants are "parity unpinned"
-// (Mip-Splatting's text is not available here).
+// at 0.  The anti-aliasing compensation o * sqrt(det Sigma_2D / det(Sigma_2D +
+// eps2d I)) is a reading of the Mip-Splatting 2D filter named in Sec. 4.1;
+// the tests pin the factor itself (closed forms, and the footprint integral
+// that it keeps independent of eps2d).
 //
 // Design: slow and plain.  The projection is written once as a template over
 // the scalar type; instantiated with forward-mode dual numbers it yields exact

@@ -165,6 +165,78 @@ def test_projection_rotated_anisotropic():
     assert p[oracle.P_SYY] == pytest.approx(S[1, 1], rel=1e-6)
 
 
+# ------------------------------------------------------------------ anti-aliasing compensation
+# Sec. 4.1 names the Mip-Splatting anti-aliasing; its 2D filter dilates the
+# screen covariance by eps2d I and scales the opacity by
+# sqrt(det Sigma_2D / det(Sigma_2D + eps2d I)), so that the footprint keeps
+# the integral it had before the dilation.  The pins below fix that factor
+# from outside the oracle: its value at eps2d = 0, two closed forms, and the
+# integral it preserves.
+def test_aa_eps_zero_is_plain_bitwise():
+    """With eps2d = 0 the dilated and the plain covariance are the same
+    numbers, so the factor is exactly 1: AA on gives the AA-off records bit
+    for bit."""
+    s = scenes.box_scene(300, 3, sh_degree=1)
+    cam = scenes.identity_camera(128, 96)
+    p0, v0 = oracle.project(s, cam, dict(eps2d=0.0, antialias=0))
+    p1, v1 = oracle.project(s, cam, dict(eps2d=0.0, antialias=1))
+    assert v0.sum() > 100 and np.array_equal(v0, v1)
+    assert np.array_equal(p0, p1)
+
+
+@pytest.mark.parametrize("eps", [0.05, 0.3, 2.0])
+def test_aa_isotropic_on_axis_closed_form(eps):
+    """Isotropic s at depth z on the axis: Sigma_2D = v I with v = (f s / z)^2,
+    so the factor is sqrt(v^2 / (v + eps)^2) = v / (v + eps)."""
+    s, z, f, o = _f(0.02), 3.0, 100.0, _f(0.9)
+    sc = _one((0, 0, z), (s, s, s), (1, 0, 0, 0), o=o)
+    v = (f * s / z) ** 2
+    p_on = oracle.project(sc, _cam(f=f), dict(eps2d=eps, antialias=1))[0][0]
+    p_off = oracle.project(sc, _cam(f=f), dict(eps2d=eps, antialias=0))[0][0]
+    assert p_off[oracle.P_O] == pytest.approx(o, abs=0)
+    assert p_on[oracle.P_O] == pytest.approx(o * v / (v + eps), rel=1e-12)
+    # the support radius follows the compensated opacity (Eq. 12, alpha_min)
+    rho = 2.5 * (1 - (1 / 255) / (o * v / (v + eps)))
+    assert p_on[oracle.P_RHO2] == pytest.approx(rho * rho, rel=1e-10)
+
+
+@pytest.mark.parametrize("th", [0.0, 0.7, 2.1])
+def test_aa_rotated_anisotropic_det_ratio(th):
+    """Scales (s1, s2) rotated by th about the axis: Sigma_2D has eigenvalues
+    a = (f s1 / z)^2 and b = (f s2 / z)^2 whatever th, so the factor is
+    sqrt(a b / ((a + eps)(b + eps)))."""
+    z, f, eps, o = 4.0, 120.0, 0.3, _f(0.6)
+    s1, s2, s3 = _f(0.08), _f(0.01), _f(0.05)
+    q = (_f(math.cos(th / 2)), 0.0, 0.0, _f(math.sin(th / 2)))
+    sc = _one((0, 0, z), (s1, s2, s3), q, o=o)
+    p = oracle.project(sc, _cam(f=f), dict(eps2d=eps, antialias=1))[0][0]
+    a, b = (f * s1 / z) ** 2, (f * s2 / z) ** 2
+    assert p[oracle.P_O] == pytest.approx(o * math.sqrt(a * b / ((a + eps) * (b + eps))), rel=1e-6)
+
+
+def test_aa_preserves_the_footprint_integral():
+    """What the compensation is for: the image-plane integral of alpha,
+    o_eff * (pi lambda^2 / 3) * sqrt(det Sigma_d) for the linear kernel, does
+    not change with eps2d; it is o (pi lambda^2 / 3) sqrt(det Sigma_2D).
+    Checked on the rendered alpha = 1 - T of one primitive (no alpha_min cut,
+    alpha below the clamp), summed over unit pixels."""
+    s1, s2, z, f, o = _f(0.3), _f(0.12), 4.0, 100.0, _f(0.5)
+    th = 0.4
+    q = (_f(math.cos(th / 2)), 0.0, 0.0, _f(math.sin(th / 2)))
+    sc = _one((0, 0, z), (s1, s2, s1), q, o=o)
+    cam = _cam(w=160, h=160, f=f, cx=80.25, cy=79.6)
+    a, b = (f * s1 / z) ** 2, (f * s2 / z) ** 2
+    want = o * (math.pi * 2.5 ** 2 / 3.0) * math.sqrt(a * b)
+    sums = []
+    for eps in (0.0, 0.3, 1.0, 4.0):
+        out = oracle.render_scene(sc, cam, dict(eps2d=eps, antialias=1, alpha_min=0.0))
+        sums.append((1.0 - out["T"]).sum())
+    assert sums == pytest.approx([want] * 4, rel=2e-3)
+    # without the compensation the integral grows with the dilation
+    plain = (1.0 - oracle.render_scene(sc, cam, dict(eps2d=4.0, antialias=0, alpha_min=0.0))["T"]).sum()
+    assert plain > 1.2 * want
+
+
 def test_projection_off_axis_jacobian():
     """Isotropic s at (x0, 0, z): J = [[f/z, 0, -f x0/z^2], [0, f/z, 0]] so
     Sigma_2D = s^2 J J^T, centre at (f x0 / z + cx, cy)."""
