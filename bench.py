@@ -29,13 +29,12 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "diff_3m_1080p"
 METRIC = "1080p fwd+bwd iters/s at 3M prims (fwd frames/s alongside)"
-SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 LANES_PER_SM = 128
 
-# DRAM traffic per launch of the dominant kernel from one ncu capture
-# (profiles/blend_bwd_3m_1080p.md: dram__bytes_read.sum + dram__bytes_write.sum),
-# valid only while the kernel source is the one measured.
+# DRAM traffic per launch of the dominant kernel from one ncu capture of the
+# bench workload (dram__bytes_read.sum + dram__bytes_write.sum), valid only
+# while the kernel source is the one measured (sha1 prefix of the file).
 NCU_TRAFFIC = {"blend_bwd": {"bytes": 71516416 + 1512704, "src": "881a35ccc7d9"}}
 
 
@@ -119,6 +118,61 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class Peaks:
+    """Roofline denominators: the measured HBM copy rate (MEASURED_PEAKS.json)
+    and the FP32 lane rate SMs x 128 lanes x the maximum SM clock, the SM
+    count read from the device; the library's dependent-free FMA probe
+    measures the latter beside it."""
+
+    def __init__(self, dev):
+        import torch
+        self.hbm, self.hbm_src = _peaks()
+        self.sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        self.alu = self.sms * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12  # Tops/s, FP32 lane instructions
+        self.alu_src = "%d SMs x %d FP32 lanes x %.0f MHz" % (self.sms, LANES_PER_SM, SM_MAX_MHZ)
+        self.fma_probe = measure_fp32_issue(dev)
+
+    def entry(self, bound, amount, ms):
+        """Roofline object of `amount` bytes (hbm) or FP32 lane operations
+        (alu) done in `ms` milliseconds."""
+        sec = ms * 1e-3
+        if bound == "hbm":
+            a = amount / sec / 1e9
+            return {"bound": "hbm", "achieved": a, "peak": self.hbm, "unit": "GB/s", "frac": a / self.hbm,
+                    "peak_source": self.hbm_src}
+        a = amount / sec / 1e12
+        return {"bound": "alu", "achieved": a, "peak": self.alu, "unit": "Tops/s", "frac": a / self.alu,
+                "peak_source": self.alu_src}
+
+    def lower_bound_ms(self, units):
+        """Time of a set of stages if each ran at its roofline."""
+        return sum(amount / (self.hbm * 1e9 if b == "hbm" else self.alu * 1e12) * 1e3 for b, amount in units)
+
+
+def frame_units(R, n_vis, K, n_eval, n_contrib, tiles, kp, sh_bytes=192):
+    """Algorithmic work of each kernel of one frame: bytes for the
+    HBM-bound stages, FP32 lane operations for the blends.  R records, n_vis
+    visible, K tile keys, n_eval evaluated and n_contrib composited pairs."""
+    par = 32 + sh_bytes  # scales, quaternion, opacity + SH of a visible primitive
+    return {
+        # mu for every record, parameters + SH of the visible ones, the 68 B record written (Sec. 3.1 Eq. 1-4)
+        "project": ("hbm", 12 * R + (par + 68) * n_vis),
+        # depth sort (histogram + 4 passes of 16 B), box per record (order, depth key, footprint, box), key
+        # count with stash (box, order, record geometry, 8 B per key written), copy to offsets (8 B read and
+        # written per key), tile sort (kp passes of 16 B per key), ranges
+        "duplicate_sort": ("hbm", 4 * R + 4 * 16 * R + (16 * R + 16 * n_vis) + (12 * R + 32 * n_vis + 8 * K)
+                           + 16 * K + kp * 16 * K + 8 * tiles),
+        # FP32 lane operations: 7 per evaluated pair, 11 more per composited pair
+        "blend_fwd": ("alu", 7 * n_eval + 11 * n_contrib),
+        # recompute 7 per evaluated pair + 40 per contributing pair
+        "blend_bwd": ("alu", 7 * n_eval + 40 * n_contrib),
+        # parameters + SH and g2d read, gradients of the same size written
+        "project_bwd": ("hbm", (2 * (12 + par) + 48 + 4) * R),
+        # 48 B per record cleared
+        "g2d_clear": ("hbm", 48 * R),
+    }
+
+
 def dist_setup(args, backend="nccl"):
     """Rank layout from the torchrun environment; one process group over all
     ranks when there is more than one (nccl on the GPUs; gloo in CPU tests)."""
@@ -162,52 +216,59 @@ def job_rate(ws, ms_per_step):
 # --------------------------------------------------------------------------
 # the oracle on the host cores (cpu_baseline leg and the reference arm)
 # --------------------------------------------------------------------------
-def oracle_frame_estimate(scene, cam, P, ncores, win=48, prim_sample=4000, seed=0):
+def oracle_frame_estimate(scene, cam, P, ncores, frac=0.1, seed=0):
     """Seconds the FP64 oracle needs for one fwd+bwd frame, from a bounded
-    sample: full projection and full tile lists, blending forward and
-    backward on a win x win pixel window scaled by the pixel fraction, and
-    the projection adjoint on a random primitive sample scaled by count."""
+    sample: the full projection and the full tile lists, then the blend
+    forward and backward on a seeded random `frac` of the tiles and the
+    projection adjoint on the same fraction of the visible primitives, each
+    scaled to the whole frame.  Returns (estimate, what was sampled, seconds
+    actually spent)."""
     import numpy as np
     import oracle
     oracle.set_threads(ncores)
     W, H = cam["width"], cam["height"]
+    tw, th = P.get("tile_w", 16), P.get("tile_h", 16)
+    tiles = ((W + tw - 1) // tw) * ((H + th - 1) // th)
+    rng = np.random.default_rng(seed)
+    mask = np.zeros(tiles, np.uint8)
+    mask[rng.choice(tiles, size=max(1, int(round(frac * tiles))), replace=False)] = 1
+    f_tiles = mask.sum() / tiles
     t0 = time.perf_counter()
     proj, vis = oracle.project(scene, cam, P)
     t_proj = time.perf_counter() - t0
-    x0, y0 = W // 2 - win // 2, H // 2 - win // 2
-    window = (x0, x0 + win, y0, y0 + win)
-    empty = (0, 0, 0, 0)
     t0 = time.perf_counter()
-    oracle.render(proj, vis, W, H, P, window=empty)
+    oracle.render(proj, vis, W, H, P, tile_mask=np.zeros(tiles, np.uint8))  # the tile lists alone
     t_lists = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.render(proj, vis, W, H, P, window=window)
-    t_fwd_win = time.perf_counter() - t0
-    rng = np.random.default_rng(seed)
+    oracle.render(proj, vis, W, H, P, tile_mask=mask)
+    t_fwd = time.perf_counter() - t0
     gC = rng.standard_normal((H, W, 3))
     gT = rng.standard_normal((H, W))
     t0 = time.perf_counter()
-    g2d = oracle.render_bwd(proj, vis, W, H, gC, gT, P, window=window)
-    t_bwd_win = time.perf_counter() - t0
+    oracle.render_bwd(proj, vis, W, H, gC, gT, P, tile_mask=mask)
+    t_bwd = time.perf_counter() - t0
     vis_idx = np.nonzero(vis)[0]
-    pick = rng.choice(vis_idx, size=min(prim_sample, len(vis_idx)), replace=False)
+    pick = np.sort(rng.choice(vis_idx, size=max(1, int(round(frac * len(vis_idx)))), replace=False))
     sub = scene.subset(pick)
     g2s = rng.standard_normal((len(pick), 9))
     t0 = time.perf_counter()
     oracle.project_bwd(sub, cam, g2s, P)
     t_pbwd = time.perf_counter() - t0
-    frac = (win * win) / float(W * H)
-    est = (t_proj + t_lists + max(t_fwd_win - t_lists, 0.0) / frac + t_lists + max(t_bwd_win - t_lists, 0.0) / frac
-           + t_pbwd * len(vis_idx) / len(pick))
-    sample = ("full projection and tile lists; blending fwd+bwd on a %dx%d window (%.5f of the pixels) and the "
-              "projection adjoint on %d of %d visible primitives, each scaled to the frame" %
-              (win, win, frac, len(pick), len(vis_idx)))
-    spent = t_proj + t_lists + t_fwd_win + t_bwd_win + t_pbwd
+    f_prims = len(pick) / len(vis_idx)
+    est = (t_proj + t_lists + max(t_fwd - t_lists, 0.0) / f_tiles + t_lists + max(t_bwd - t_lists, 0.0) / f_tiles
+           + t_pbwd / f_prims)
+    sample = ("full projection and tile lists; blending fwd+bwd on a seeded random %.3f of the tiles (%d of %d) and "
+              "the projection adjoint on %d of %d visible primitives, each scaled to the frame" %
+              (f_tiles, int(mask.sum()), tiles, len(pick), len(vis_idx)))
+    spent = t_proj + 2 * t_lists + t_fwd + t_bwd + t_pbwd
     return est, sample, spent
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle as it stands on the host cores."""
+    """Reference arm: the FP64 oracle as it stands on the host cores.  Each
+    step is one bounded sample of the frame (oracle_frame_estimate); the line
+    reports the seconds a step really took as ms_per_step and the frame rate
+    the sample extrapolates to as value."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -218,24 +279,28 @@ def run_reference(args):
     ncores = os.cpu_count() or 1
     scene, cams, extra = scenes.make_workload(WORKLOAD)
     P = dict(sh_degree=3, antialias=int(extra["antialias"]))
-    # each step is the bounded sample of the cpu_baseline leg (~6 s of host
-    # work); at most 3 warm-up and 3 timed steps keep the run near a minute
-    steps, warmup = min(args.steps, 3), min(args.warmup, 3)
-    ests = []
+    # a sample is several seconds of host work: at most one warm-up and three
+    # timed steps keep the arm within a minute or two
+    steps, warmup = max(1, min(args.steps, 3)), min(args.warmup, 1)
+    ests, spent = [], []
     sample = ""
     for i in range(warmup + steps):
-        est, sample, _ = oracle_frame_estimate(scene, cams[0], P, ncores, seed=i)
+        t0 = time.perf_counter()
+        est, sample, _ = oracle_frame_estimate(scene, cams[0], P, ncores)
         if i >= warmup:
             ests.append(est)
+            spent.append(time.perf_counter() - t0)
     sec = statistics.median(ests)
     value = 1.0 / sec
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws,
-            "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * sec, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * statistics.mean(spent),
+            "frame_seconds_estimate": sec, "frame_seconds_estimates": [round(e, 3) for e in ests],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "prims": scene.n, "width": cams[0]["width"],
                        "height": cams[0]["height"], "sh_degree": 3},
             "cpu_baseline": {"value": value, "unit": "iters/s", "cores": ncores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "estimate": "value extrapolates the sample to the whole frame; "
+                                                           "ms_per_step is the time one sample took"},
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -271,6 +336,59 @@ def bench_batched(dev, reps=10):
     K = int(br.n_keys.item())
     del br
     torch.cuda.empty_cache()
+    # Roofline of the batched call: its projection and duplicate/sort stages
+    # timed through ls_project / ls_duplicate_sort on the same 64 cameras and
+    # tile shape; the persistent blend (with its job queue) is the rest of the
+    # call.  Blend work from the per-camera counting forward (the batched
+    # blend walks the same lists with the same per-tile code).
+    rzb = raster.Rasterizer(Pt, device=dev)
+    proj, tc = rzb.project(sp, cams, counts=True)
+    rzb.ensure_capacity(tc)
+    R = sp.n * len(cams)
+    n_vis = int((proj.view(torch.uint8)[64 * R:68 * R].view(torch.int32) != -1).sum().item())
+    del proj, tc
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_proj, t_sort = [], []
+    for i in range(4):
+        ev[0].record()
+        proj, _ = rzb.project(sp, cams, counts=False)
+        ev[1].record()
+        rzb.duplicate_sort(proj, R, cams)
+        ev[2].record()
+        torch.cuda.synchronize(dev)
+        if i:
+            t_proj.append(ev[0].elapsed_time(ev[1]))
+            t_sort.append(ev[1].elapsed_time(ev[2]))
+        del proj
+    rzb.check_status("batched stages")
+    del rzb
+    torch.cuda.empty_cache()
+    n_eval = n_contrib = tiles = 0
+    rzc = raster.Rasterizer(Pt, device=dev)
+    for cam in cams:
+        _, _, st = rzc.forward(sp, cam)
+        _, _, _, ne, nc = rzc.render_stats(st["proj"], sp.n, cam, st["ranges"], st["vals"])
+        n_eval += ne
+        n_contrib += nc
+        tiles += raster.tiles_of(cam, Pt)
+        del st
+    rzc.check_status("batched counts")
+    del rzc
+    torch.cuda.empty_cache()
+    kp = (max(1, (tiles - 1).bit_length()) + 7) // 8
+    u = frame_units(R, n_vis, K, n_eval, n_contrib, tiles, kp, sh_bytes=192)
+    ms_p, ms_s = statistics.median(t_proj), statistics.median(t_sort)
+    ms_blend = max(ms_batch - ms_p - ms_s, 1e-6)
+    peaks = Peaks(dev)
+    lb = peaks.lower_bound_ms([u["project"], u["duplicate_sort"], u["blend_fwd"]])
+    roof = {"project": peaks.entry(*u["project"], ms_p), "duplicate_sort": peaks.entry(*u["duplicate_sort"], ms_s),
+            "blend": dict(peaks.entry(*u["blend_fwd"], ms_blend),
+                          timing="the call's time less the projection and duplicate/sort stages"),
+            "frame": {"lower_bound_ms": lb, "frac": lb / ms_batch,
+                      "meaning": "time of the call's stages at their rooflines over its measured time"}}
+    roof = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in r.items()} for k, r in roof.items()}
+    units_b = {"records": R, "visible": n_vis, "pairs_evaluated": n_eval, "pairs_composited": n_contrib,
+               "tiles": tiles}
     # the plain path, one camera at a time, at the faster of the tuned tile
     # shape and its default 16x16
     plain_ms = {}
@@ -296,7 +414,7 @@ def bench_batched(dev, reps=10):
             "ms_per_batch": ms_batch, "frames_per_s": len(cams) * 1e3 / ms_batch,
             "plain_ms_per_batch": ms_plain, "plain_frames_per_s": len(cams) * 1e3 / ms_plain,
             "plain_tile": plain_tile, "plain_ms_by_tile": {k: round(v, 3) for k, v in plain_ms.items()},
-            "speedup_vs_plain": ms_plain / ms_batch,
+            "speedup_vs_plain": ms_plain / ms_batch, "roofline": roof, "units": units_b,
             "autotune_ms": {"%dx%d/b%d" % k: round(v, 3) for k, v in tune.table.items()}}
 
 
@@ -313,7 +431,8 @@ def time_frame(sp, cam, P, dev, steps=20, warmup=3):
     H, W = cam["height"], cam["width"]
     w, v = scenes.loss_weights(H, W, seed=7)
     gimg, gT = torch.from_numpy(w).to(dev), torch.from_numpy(v).to(dev)
-    g2d = torch.empty((R, 12), dtype=torch.float32, device=dev)
+    gout = dict(means=torch.empty_like(sp.means), scales=torch.empty_like(sp.scales),
+                quats=torch.empty_like(sp.quats), opac=torch.empty_like(sp.opac), sh=torch.empty_like(sp.sh))
     proj, tc = rz.project(sp, [cam], counts=True)
     rz.ensure_capacity(tc)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
@@ -326,9 +445,7 @@ def time_frame(sp, cam, P, dev, steps=20, warmup=3):
         image, T, n_last = rz.render_fwd(proj, R, cam, ranges, vals)
         if e:
             e[1].record()
-        g2d.zero_()
-        rz.blend_bwd(proj, R, cam, ranges, vals, T, n_last, gimg, gT, g2d)
-        rz.project_bwd(sp, [cam], proj, g2d)
+        rz.render_bwd(sp, cam, dict(proj=proj, ranges=ranges, vals=vals, T=T, n_last=n_last), gimg, gT, out=gout)
         if e:
             e[2].record()
     torch.cuda.synchronize(dev)
@@ -421,6 +538,28 @@ def bench_learned(dev, reps=20):
                      "tiles_refuted": refuted, "psnr_db": psnr(lr.image, img0),
                      "max_abs_err": float((lr.image - img0).abs().max().item())}
     out["tiles"] = lr.tiles
+    del lr
+    torch.cuda.empty_cache()
+    # Frame-level roofline of the learned frame: its projection, its sort
+    # stages over the keys it actually sorted (kept + held out) and a blend
+    # of the work a plain render stopping at t_thr counts, each at its
+    # roofline, over the measured frame time.
+    rzs = raster.Rasterizer(raster.RenderParams(sh_degree=3, t_min=t_thr), device=dev)
+    _, _, st = rzs.forward(sp, cam)
+    _, _, _, ne, nc = rzs.render_stats(st["proj"], sp.n, cam, st["ranges"], st["vals"])
+    R = sp.n
+    n_vis = int((st["proj"].view(torch.uint8)[64 * R:68 * R].view(torch.int32) != -1).sum().item())
+    rzs.check_status("learned counts")
+    del rzs, st
+    torch.cuda.empty_cache()
+    u = frame_units(R, n_vis, out["mlp"]["keys_sorted"], ne, nc, out["tiles"], 2, sh_bytes=192)
+    peaks = Peaks(dev)
+    lb = peaks.lower_bound_ms([u["project"], u["duplicate_sort"], u["blend_fwd"]])
+    out["roofline"] = {"frame": {"lower_bound_ms": round(lb, 4), "frac": round(lb / out["mlp"]["ms"], 4),
+                                 "meaning": "time of projection, the sort of the keys sorted and the blend at their "
+                                            "rooflines over the measured learned frame"},
+                       "units": {"visible": n_vis, "keys_sorted": out["mlp"]["keys_sorted"],
+                                 "pairs_evaluated_at_t_thr": ne, "pairs_composited_at_t_thr": nc}}
     out["speedup_vs_plain"] = out["plain"]["ms"] / out["mlp"]["ms"]
     out["speedup_vs_keep_all"] = out["keep_all"]["ms"] / out["mlp"]["ms"]
     if const is not None:
@@ -502,9 +641,10 @@ def main():
     gout = dict(means=torch.empty_like(sp.means), scales=torch.empty_like(sp.scales),
                 quats=torch.empty_like(sp.quats), opac=torch.empty_like(sp.opac), sh=torch.empty_like(sp.sh))
 
-    # g2d_clear (the zeroed gradient buffer the backward accumulates into) is
-    # timed apart so that blend_bwd brackets that one kernel
-    stage_names = ["project", "duplicate_sort", "blend_fwd", "g2d_clear", "blend_bwd", "project_bwd"]
+    # One step is the boundary calls of the frame: ls_project,
+    # ls_duplicate_sort, ls_render_fwd and ls_render_bwd (which clears its
+    # 2D-gradient buffer itself and runs the blend and projection adjoints).
+    stage_names = ["project", "duplicate_sort", "render_fwd", "render_bwd"]
 
     def step(evs=None, bwd=True, splats=None, grad_image=None, grad_t=None, outg=None):
         spx = splats or sp
@@ -518,14 +658,32 @@ def main():
         rec(3)
         if not bwd:
             return image, T, None
-        g2d.zero_()
+        state = dict(proj=proj, ranges=ranges, vals=vals, T=T, n_last=n_last)
+        g = rz.render_bwd(spx, cam, state, grad_image if grad_image is not None else gimg,
+                          grad_t if grad_t is not None else gT, out=outg or gout)
         rec(4)
-        rz.blend_bwd(proj, R, cam, ranges, vals, T, n_last, grad_image if grad_image is not None else gimg,
-                     grad_t if grad_t is not None else gT, g2d)
-        rec(5)
-        g = rz.project_bwd(spx, [cam], proj, g2d, out=outg or gout)
-        rec(6)
         return image, T, g
+
+    # The same frame kernel by kernel, for the per-kernel durations of the
+    # rooflines: the adjoint as ls_blend_bwd into a cleared 2D-gradient buffer
+    # (cleared by a device copy through ls_copy) and ls_project_bwd.
+    kernel_names = ["project", "duplicate_sort", "blend_fwd", "g2d_clear", "blend_bwd", "project_bwd"]
+    g2d_zero = torch.zeros((R, 12), dtype=torch.float32, device=dev)
+
+    def kernel_step(evs):
+        evs[0].record()
+        proj, _ = rz.project(sp, [cam], counts=False)
+        evs[1].record()
+        keys, vals, n_keys, ranges = rz.duplicate_sort(proj, R, [cam])
+        evs[2].record()
+        image, T, n_last = rz.render_fwd(proj, R, cam, ranges, vals)
+        evs[3].record()
+        raster.copy_(g2d, g2d_zero)
+        evs[4].record()
+        rz.blend_bwd(proj, R, cam, ranges, vals, T, n_last, gimg, gT, g2d)
+        evs[5].record()
+        rz.project_bwd(sp, [cam], proj, g2d, out=gout)
+        evs[6].record()
 
     # capacity from an exact count, then no host syncs inside steps
     proj, tc = rz.project(sp, [cam], counts=True)
@@ -558,6 +716,19 @@ def main():
     total_ms = max_over_ranks(t_start.elapsed_time(t_end), ws)
     rz.check_status("timed steps")
     stage_ms = {nm: statistics.mean(e[j].elapsed_time(e[j + 1]) for e in evs) for j, nm in enumerate(stage_names)}
+
+    # ---------------------------------------------------------------- kernel by kernel
+    kevs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(kernel_names) + 1)] for _ in range(args.steps)]
+    for _ in range(2):
+        kernel_step(kevs[0])
+    torch.cuda.synchronize()
+    with ClockSampler(local) as kclocks:
+        for i in range(args.steps):
+            kernel_step(kevs[i])
+        torch.cuda.synchronize()
+    rz.check_status("kernel by kernel")
+    kernel_ms = {nm: statistics.mean(e[j].elapsed_time(e[j + 1]) for e in kevs)
+                 for j, nm in enumerate(kernel_names)}
 
     # ---------------------------------------------------------------- timed fwd only
     barrier(ws)
@@ -665,72 +836,47 @@ def main():
     value = job_rate(ws, ms)
 
     # ---------------------------------------------------------------- roofline of the dominant kernel
-    hbm_peak, peak_src = _peaks()
-    alu_peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12  # Tops/s, FP32 lane instructions
-    fma_probe = measure_fp32_issue(dev)  # the same rate measured with the library's dependent-free FMA probe
+    peaks = Peaks(dev)
     kp = 2
     nt = raster.tiles_of(cam, P)
-    units = {
-        # bytes: mu for all, params + SH3 for visible, 68 B record written (Sec. 3.1 Eq. 1-4)
-        "project": ("hbm", 12 * R + (224 + 68) * n_vis),
-        # depth sort (histogram + 4 passes of 16 B), box per record (order, depth key, footprint, box), key
-        # count with stash (box, order, record geometry, 8 B per key written), copy to offsets (8 B read and
-        # written per key), tile sort (kp passes of 16 B per key), ranges
-        "duplicate_sort": ("hbm", 4 * R + 4 * 16 * R + (16 * R + 16 * n_vis) + (12 * R + 32 * n_vis + 8 * K)
-                           + 16 * K + kp * 16 * K + 8 * nt),
-        # FP32 lane operations: 7 per evaluated pair, 11 more per composited pair
-        "blend_fwd": ("alu", 7 * n_eval + 11 * n_contrib),
-        # recompute 7 per evaluated pair + 40 per contributing pair
-        "blend_bwd": ("alu", 7 * n_eval + 40 * n_contrib),
-        # params + SH3 and g2d read, 236 B of gradients written
-        "project_bwd": ("hbm", (236 + 48 + 4 + 236) * R),
-        # 48 B per record zeroed
-        "g2d_clear": ("hbm", 48 * R),
-    }
-
-    def roofline_of(stage):
-        bound, amount = units[stage]
-        sec = stage_ms[stage] * 1e-3
-        if bound == "hbm":
-            achieved = amount / sec / 1e9
-            return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "peak_source": peak_src}
-        achieved = amount / sec / 1e12
-        return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz"}
-
+    units = frame_units(R, n_vis, K, n_eval, n_contrib, nt, kp, sh_bytes=192)
+    stage_roofs = {k: peaks.entry(*units[k], kernel_ms[k]) for k in kernel_names}
     # the dominant kernel: the longest stage that is one launch (duplicate_sort
     # is a chain of a dozen launches, none of them longer than the blends)
-    dom = max((k for k in stage_ms if k not in ("duplicate_sort", "g2d_clear")), key=lambda k: stage_ms[k])
-    roof = roofline_of(dom)
+    dom = max((k for k in kernel_ms if k not in ("duplicate_sort", "g2d_clear")), key=lambda k: kernel_ms[k])
+    roof = dict(stage_roofs[dom])
     if roof["bound"] == "alu":
-        roof["peak_check"] = {"measured_fma_tops": round(fma_probe, 3), "of_peak": round(fma_probe / alu_peak, 4)}
-    stage_roofs = {k: {"bound": r["bound"], "achieved": round(r["achieved"], 3), "unit": r["unit"],
-                       "frac": round(r["frac"], 4)} for k, r in ((k, roofline_of(k)) for k in stage_ms)}
+        roof["peak_check"] = {"measured_fma_tops": round(peaks.fma_probe, 3),
+                              "of_peak": round(peaks.fma_probe / peaks.alu, 4)}
     tr = NCU_TRAFFIC.get(dom)
     src = {"blend_fwd": "blend.cu", "blend_bwd": "blend.cu", "project": "project.cu", "project_bwd": "project.cu",
            "duplicate_sort": "sort.cu"}[dom]
     roof["kernel"] = dom
+    roof["duration_ms"] = kernel_ms[dom]
+    roof["timing"] = ("CUDA events around the kernel's launch on its stream, mean over %d kernel-by-kernel steps of "
+                      "the same frame" % args.steps)
     roof["traffic"] = tr["bytes"] if tr and tr.get("src") == _src_hash(src) else None
+    stage_roofs = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in r.items()
+                       if kk in ("bound", "achieved", "unit", "frac")} for k, r in stage_roofs.items()}
 
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if args.prims is None else "%s (prims=%d)" % (WORKLOAD, R), "prims": R,
-                   "width": W, "height": H, "sh_degree": 3,
+                       "width": W, "height": H, "sh_degree": 3,
                        "tile": "%dx%d" % (P.tile_w, P.tile_h), "l2": "inputs larger than L2 (708 MB of parameters)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "fwd_fps": job_rate(ws, fwd_ms), "fwd_ms": fwd_ms,
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "kernels_ms": {k: round(v, 4) for k, v in kernel_ms.items()},
             "stage_rooflines": stage_roofs,
             "units": {"tile_keys": K, "box_tile_keys": K_box, "visible": n_vis, "pairs_evaluated": n_eval,
                       "pairs_composited": n_contrib},
-            "roofline": roof, "clocks": clocks.summary(), "e2e": e2e,
-            # per step: project 1; duplicate_sort 12 + kp (depth histogram, scan, 4 passes, boxes, key count,
-            # scan, key copy, digit scan, kp tile passes, ranges); blend fwd, blend bwd, project bwd 1 each
-            # per step: project; histogram, scan, 4 depth passes, boxes, key count, 2-launch warp-count
-            # scan, key copy, digit scan, kp tile passes, ranges; blend_fwd, blend_bwd, project_bwd
-            "gpu_launches": args.steps * (1 + (13 + kp) + 3)}
+            "roofline": roof, "clocks": clocks.summary(), "clocks_kernel_by_kernel": kclocks.summary(), "e2e": e2e,
+            # per step: ls_project 1; ls_duplicate_sort 13 + kp (depth histogram, scan, 4 depth passes, boxes,
+            # key count, 2-launch warp-count scan, key copy, digit scan, kp tile passes, ranges); ls_render_fwd
+            # 1; ls_render_bwd 2 (blend adjoint, projection adjoint; its clear is a memset)
+            "gpu_launches": args.steps * (1 + (13 + kp) + 1 + 2)}
 
     if not args.no_batch and args.prims is None:
         line["batched"] = bench_batched(dev)

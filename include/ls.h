@@ -341,6 +341,17 @@ ls_status ls_copy(void* dst, const void* src, size_t bytes, void* stream);
  * only to keep the chains live). */
 ls_status ls_fp32_issue_probe(int64_t iters, int32_t blocks_per_sm, float* out, int64_t* lane_ops, void* stream);
 
+/* For tests of failure detection: the onesweep radix sort's look-back waits
+ * on its predecessor partitions, each wait bounded by spin_limit polls (0
+ * restores the default, about a second); after that it writes
+ * LS_ERR_TIMEOUT to status_dev and the pass finishes with in-bounds writes
+ * (its output order is then unspecified).  hold_partition >= 0 makes that
+ * partition of the last pass of every tile sort publish nothing, so the
+ * wait of the partition after it runs out on purpose; -1 turns that off.
+ * Process-wide, not thread-safe; LS_ERR_INVALID_ARG for spin_limit < 0 or
+ * hold_partition < -1. */
+ls_status ls_debug_set_sort_wait(int32_t spin_limit, int32_t hold_partition);
+
 /* Text of a status code (static storage). */
 const char* ls_status_string(int32_t status);
 

@@ -114,10 +114,19 @@ def _window(window):
     return _p(w), w
 
 
-def render(proj, vis, width, height, params=None, rule_f32=False, dkey=None, brute=False, window=None):
+def _mask(tile_mask):
+    if tile_mask is None:
+        return ctypes.c_void_p(0), None
+    m = np.ascontiguousarray(tile_mask, dtype=np.uint8)
+    return _p(m), m
+
+
+def render(proj, vis, width, height, params=None, rule_f32=False, dkey=None, brute=False, window=None,
+           tile_mask=None):
     """Front-to-back composite (Eq. 6) of projected records; `window` =
-    (x0, x1, y0, y1) restricts it to those pixels (others stay zero).
-    Also returns per-tile termination depths `labels` (tiled mode)."""
+    (x0, x1, y0, y1) restricts it to those pixels (others stay zero), and
+    `tile_mask` [tiles] to the tiles where it is set.  Also returns per-tile
+    termination depths `labels` (tiled mode)."""
     n = proj.shape[0]
     proj = _d(proj)
     vis8 = np.ascontiguousarray(vis, dtype=np.uint8)
@@ -129,6 +138,7 @@ def render(proj, vis, width, height, params=None, rule_f32=False, dkey=None, bru
     stats = np.zeros(2, dtype=np.int64)
     dk = None if dkey is None else np.ascontiguousarray(dkey, dtype=np.uint32)
     wp, _keep = _window(window)
+    mp, _mkeep = _mask(tile_mask)
     Pd = dict(DEFAULTS)
     Pd.update(params or {})
     tiles = ((width + Pd["tile_w"] - 1) // Pd["tile_w"]) * ((height + Pd["tile_h"] - 1) // Pd["tile_h"])
@@ -136,7 +146,7 @@ def render(proj, vis, width, height, params=None, rule_f32=False, dkey=None, bru
     lib().lso_render(ctypes.c_int(n), _p(proj), _p(vis8), ctypes.c_int(width), ctypes.c_int(height),
                      _p(params_array(params)), ctypes.c_int(int(rule_f32)),
                      _p(dk) if dk is not None else ctypes.c_void_p(0), ctypes.c_int(int(brute)), _p(img), _p(T),
-                     _p(n_last), _p(last_id), _p(flags), _p(stats), wp, _p(labels))
+                     _p(n_last), _p(last_id), _p(flags), _p(stats), wp, _p(labels), mp)
     return dict(image=img, T=T, n_last=n_last, last_id=last_id, flags=flags.astype(bool), n_eval=int(stats[0]),
                 n_contrib=int(stats[1]), labels=labels)
 
@@ -155,17 +165,19 @@ def tile_depth_hist(foot, dkey, proj, width, height, tile_w, tile_h):
     return counts, cov
 
 
-def render_bwd(proj, vis, width, height, gC, gT, params=None, rule_f32=False, dkey=None, window=None):
+def render_bwd(proj, vis, width, height, gC, gT, params=None, rule_f32=False, dkey=None, window=None,
+               tile_mask=None):
     """Adjoint of `render` with respect to (mx, my, a, b, c, o_eff, r, g, b);
-    with `window` only those pixels' terms are summed."""
+    with `window` (`tile_mask`) only those pixels' (tiles') terms are summed."""
     n = proj.shape[0]
     g2d = np.zeros((n, 9))
     dk = None if dkey is None else np.ascontiguousarray(dkey, dtype=np.uint32)
     wp, _keep = _window(window)
+    mp, _mkeep = _mask(tile_mask)
     lib().lso_render_bwd(ctypes.c_int(n), _p(_d(proj)), _p(np.ascontiguousarray(vis, dtype=np.uint8)),
                          ctypes.c_int(width), ctypes.c_int(height), _p(params_array(params)),
                          ctypes.c_int(int(rule_f32)), _p(dk) if dk is not None else ctypes.c_void_p(0),
-                         _p(_d(gC)), _p(_d(gT)), _p(g2d), wp)
+                         _p(_d(gC)), _p(_d(gT)), _p(g2d), wp, mp)
     return g2d
 
 

@@ -700,9 +700,12 @@ void lso_tile_depth_hist(long long R, const float* foot, const uint32_t* dkey, c
 // background), T [H][W], n_last (tile-list count), last_id, flags, stats[0] =
 // evaluated pairs, stats[1] = composited pairs.  window (NULL = whole image):
 // {x0, x1, y0, y1}, only pixels in [x0, x1) x [y0, y1) are composited.
+// tile_mask (NULL = every tile): only tiles with a non-zero entry are
+// composited (a sample of the frame, for timing).
 int lso_render(int n, const double* proj, const unsigned char* vis, int W, int H, const double* parv,
                int rule_f32, const uint32_t* dkey, int brute, double* image, double* T, int32_t* n_last,
-               int32_t* last_id, unsigned char* flags, long long* stats, const int32_t* window, double* labels) {
+               int32_t* last_id, unsigned char* flags, long long* stats, const int32_t* window, double* labels,
+               const unsigned char* tile_mask) {
   Par P = unpack_par(parv);
   // pixel window [x0, x1) x [y0, y1); pixels outside it are left untouched
   int wx0 = window ? window[0] : 0, wx1 = window ? window[1] : W;
@@ -734,6 +737,7 @@ int lso_render(int n, const double* proj, const unsigned char* vis, int W, int H
   int ntiles = Ls.tiles_x * Ls.tiles_y;
 #pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1) reduction(+ : n_eval, n_contrib)
   for (int t = 0; t < ntiles; ++t) {
+    if (tile_mask && !tile_mask[t]) continue;
     int tx = t % Ls.tiles_x, ty = t / Ls.tiles_x;
     int emax = 0, npix = 0, smax = -1;
     bool never = false;
@@ -771,10 +775,10 @@ int lso_render(int n, const double* proj, const unsigned char* vis, int W, int H
 // g2d [n][9] = d/d(mx, my, a, b, c, o_eff, r, g, b).  gC [H][W][3], gT [H][W].
 // Forward transmittances are kept per pixel, not recomputed.  With ags != 0
 // the kernel-derivative path is scaled by w(D) (Eq. 13-14), so the result is
-// no longer an exact gradient.
+// no longer an exact gradient.  window and tile_mask as for lso_render.
 int lso_render_bwd(int n, const double* proj, const unsigned char* vis, int W, int H, const double* parv,
                    int rule_f32, const uint32_t* dkey, const double* gC, const double* gT, double* g2d,
-                   const int32_t* window) {
+                   const int32_t* window, const unsigned char* tile_mask) {
   Par P = unpack_par(parv);
   int wx0 = window ? window[0] : 0, wx1 = window ? window[1] : W;
   int wy0 = window ? window[2] : 0, wy1 = window ? window[3] : H;
@@ -783,6 +787,7 @@ int lso_render_bwd(int n, const double* proj, const unsigned char* vis, int W, i
   int ntiles = Ls.tiles_x * Ls.tiles_y;
 #pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1)
   for (int t = 0; t < ntiles; ++t) {
+    if (tile_mask && !tile_mask[t]) continue;
     int tx = t % Ls.tiles_x, ty = t / Ls.tiles_x;
     std::vector<PairRec> rec;
     for (int py = std::max(ty * P.tile_h, wy0); py < std::min(std::min(H, (ty + 1) * P.tile_h), wy1); ++py)

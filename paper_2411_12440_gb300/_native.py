@@ -76,6 +76,7 @@ PROTOTYPES = {
                              _P, _P, _P, _SZ, _P, _P]),
     "ls_copy": (_I32, [_P, _P, _SZ, _P]),
     "ls_fp32_issue_probe": (_I32, [_I64, _I32, _P, ctypes.POINTER(ctypes.c_int64), _P]),
+    "ls_debug_set_sort_wait": (_I32, [_I32, _I32]),
 }
 
 _lib = None

@@ -158,9 +158,21 @@ DupWs dup_layout(char* base, int64_t R, int64_t cap, int key_passes) {
 
 }  // namespace
 
+bool ls::host_total_tiles(const ls_camera* cams, int n_cams, const ls_params* p, int64_t* total_tiles) {
+  if (!params_ok(p)) return false;
+  CamTable T;
+  return make_cams(cams, n_cams, p, T, total_tiles);
+}
+
 extern "C" {
 
 int32_t ls_version(void) { return 1; }
+
+ls_status ls_debug_set_sort_wait(int32_t spin_limit, int32_t hold_partition) {
+  if (spin_limit < 0 || hold_partition < -1) return LS_ERR_INVALID_ARG;
+  set_sort_wait(spin_limit, hold_partition);
+  return LS_OK;
+}
 
 const char* ls_status_string(int32_t s) {
   switch (s) {

@@ -8,6 +8,29 @@
 
 namespace ls {
 
+// Multiprocessor count of the current device, read once per device.
+inline cudaError_t current_sm_count(int* out) {
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (cache[dev] == 0) {
+    e = cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  *out = cache[dev];
+  return cudaSuccess;
+}
+
+// Total tiles of a camera set under the host-side rules of the ABI (valid
+// parameters, camera sizes up to 16384, at most 2^24 tiles); false when a
+// rule is broken.
+bool host_total_tiles(const ls_camera* cams, int n_cams, const ls_params* p, int64_t* total_tiles);
+
+// Bounded waits of the onesweep look-back (ls_debug_set_sort_wait).
+void set_sort_wait(int spin_limit, int hold_part);
+
 // ---- projection (project.cu)
 cudaError_t launch_project_fwd(int n, const float* means, const float* scales, const float* quats,
                                const float* opac, const float* sh, const CamTable& cams, const ParDev& P,

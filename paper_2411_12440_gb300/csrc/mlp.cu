@@ -426,8 +426,11 @@ __global__ void __launch_bounds__(256) mlp_adam_kernel(int step, float lr, float
 cudaError_t launch_mlp_forward(int64_t m, const void* x, const MlpDev& net, float* y, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   const int64_t tiles = (m + 15) / 16;
+  int sms = 0;
+  cudaError_t e = current_sm_count(&sms);
+  if (e != cudaSuccess) return e;
   int grid = (int)((tiles + 3) / 4);
-  if (grid > 152 * 8) grid = 152 * 8;
+  if (grid > sms * 8) grid = sms * 8;
   mlp_forward_kernel<<<grid, 128, 0, st>>>(m, static_cast<const __half*>(x), static_cast<const __half*>(net.w1t),
                                            net.b1, static_cast<const __half*>(net.w2t), net.b2,
                                            static_cast<const __half*>(net.w3), net.b3, y);
@@ -448,7 +451,10 @@ cudaError_t launch_mlp_backward(int64_t m, const void* x, const MlpDev& net, con
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
   const int64_t chunks = (m + 127) / 128;
-  int grid = (int)(chunks < 152 * 2 ? chunks : 152 * 2);
+  int sms = 0;
+  e = current_sm_count(&sms);
+  if (e != cudaSuccess) return e;
+  int grid = (int)(chunks < 2 * sms ? chunks : 2 * sms);
   mlp_backward_kernel<<<grid, 256, sm, st>>>(m, static_cast<const __half*>(x), static_cast<const __half*>(net.w1t),
                                             net.b1, static_cast<const __half*>(net.w2t), net.b2,
                                             static_cast<const __half*>(net.w3), net.b3, target, under_weight,

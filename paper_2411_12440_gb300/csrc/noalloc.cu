@@ -40,16 +40,12 @@ extern "C" ls_status ls_duplicate_sort_noalloc(int64_t n_records, const void* pr
                                                int32_t n_cams, const ls_params* params, int64_t key_capacity,
                                                uint32_t* keys, uint32_t* vals, int64_t* n_keys_dev,
                                                int32_t* tile_ranges, int32_t* status_dev, void* stream) {
-  if (!params || !cams || n_cams < 1 || n_cams > LS_MAX_CAMS || params->tile_w <= 0 || params->tile_h <= 0)
-    return LS_ERR_INVALID_ARG;
-  if (n_records > LS_NOALLOC_MAX_RECORDS || key_capacity > LS_NOALLOC_MAX_KEYS) return LS_ERR_UNSUPPORTED;
+  // the tile count under ls_duplicate_sort's own parameter and camera rules
+  // (so a size that would overflow the count is rejected before it is formed)
   int64_t tiles = 0;
-  for (int c = 0; c < n_cams; ++c) {
-    if (cams[c].width <= 0 || cams[c].height <= 0) return LS_ERR_INVALID_ARG;
-    tiles += (int64_t)((cams[c].width + params->tile_w - 1) / params->tile_w) *
-             ((cams[c].height + params->tile_h - 1) / params->tile_h);
-  }
-  if (tiles < 1 || tiles > (1 << 24)) return LS_ERR_INVALID_ARG;
+  if (!ls::host_total_tiles(cams, n_cams, params, &tiles) || tiles < 1) return LS_ERR_INVALID_ARG;
+  if (n_records < 0 || key_capacity < 0) return LS_ERR_INVALID_ARG;
+  if (n_records > LS_NOALLOC_MAX_RECORDS || key_capacity > LS_NOALLOC_MAX_KEYS) return LS_ERR_UNSUPPORTED;
   const size_t need = ls_duplicate_sort_workspace(n_records, key_capacity, (int32_t)tiles);
   if (need == 0) return LS_ERR_INVALID_ARG;
   if (need > (size_t)LS_NOALLOC_SCRATCH_BYTES) return LS_ERR_UNSUPPORTED;

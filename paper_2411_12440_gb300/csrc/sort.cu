@@ -11,8 +11,8 @@
 // ranked in registers with warp ballots, published as a per-digit aggregate,
 // completed by looking back over its predecessors, staged in shared memory in
 // sorted order and written out in digit runs.  Every wait on a predecessor is
-// bounded: after SPIN_LIMIT polls the kernel records LS_ERR_TIMEOUT and
-// finishes with in-bounds writes only.
+// bounded: after a host-set number of polls (about a second at the default)
+// the kernel records LS_ERR_TIMEOUT and finishes with in-bounds writes only.
 #include "kernels.h"
 
 namespace ls {
@@ -22,7 +22,12 @@ namespace {
 constexpr uint64_t LB_AGG = 1ull << 62;
 constexpr uint64_t LB_INC = 1ull << 63;
 constexpr uint64_t LB_VAL = (1ull << 62) - 1;
-constexpr int SPIN_LIMIT = 1 << 21;
+// Bounded waits of the look-back (ls_debug_set_sort_wait): polls before a
+// wait gives up, and a partition of the last tile-sort pass that publishes
+// nothing (-1: none), so that the wait of the partition after it runs out.
+constexpr int SPIN_LIMIT_DEFAULT = 1 << 21;
+int g_spin_limit = SPIN_LIMIT_DEFAULT;
+int g_hold_part = -1;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
 static_assert(SORT_THREADS == RADIX, "one thread per digit");
 
@@ -110,7 +115,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const int64_t* n_dev, int64_t n_host, int shift,
     const uint32_t* __restrict__ digit_base, uint64_t* lookback, uint32_t* part_ctr, uint2* ranges,
-    int32_t* status) {
+    int32_t* status, int spin_limit, int hold_part) {
   constexpr uint32_t MASK = (1u << BITS) - 1u;
   constexpr int PART = SORT_THREADS * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -179,7 +184,8 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
     }
     uint64_t* my = lookback + (size_t)part * RADIX + d;
     const bool used = d <= (int)MASK;  // digits beyond the pass's width never occur
-    if (used) st_relaxed_u64(my, (part == 0 ? LB_INC : LB_AGG) | (uint64_t)run);
+    const bool publish = (int)part != hold_part;
+    if (used && publish) st_relaxed_u64(my, (part == 0 ? LB_INC : LB_AGG) | (uint64_t)run);
     const uint32_t incl = block_incl_scan(run, S.warp);
     S.local[d] = incl - run;
     uint64_t prefix = 0;
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
       while (p >= 0) {
         const uint64_t v = ld_relaxed_u64(lookback + (size_t)p * RADIX + d);
         if ((v & (LB_AGG | LB_INC)) == 0) {
-          if (++spins > SPIN_LIMIT) {
+          if (++spins > spin_limit) {
             set_status(status, LS_ERR_TIMEOUT);
             break;
           }
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
         if (v & LB_INC) break;
         --p;
       }
-      st_relaxed_u64(my, LB_INC | (prefix + run));
+      if (publish) st_relaxed_u64(my, LB_INC | (prefix + run));
     }
     S.glob[d] = digit_base[d] + (uint32_t)prefix - S.local[d];
   }
@@ -272,7 +278,10 @@ SortScratch sort_scratch_carve(void* base, int64_t cap, int passes, int items) {
 
 cudaError_t launch_radix_hist(const uint32_t* keys, const int64_t* n_dev, int64_t n_host, int begin_bit,
                               int passes, uint32_t* hist, cudaStream_t st) {
-  int blocks = 152 * 4;
+  int sms = 0;
+  cudaError_t e = current_sm_count(&sms);
+  if (e != cudaSuccess) return e;
+  const int blocks = 4 * sms;
   radix_hist_kernel<<<blocks, 256, 0, st>>>(keys, n_dev, n_host, begin_bit, passes, hist);
   return cudaGetLastError();
 }
@@ -300,17 +309,16 @@ static cudaError_t onesweep_launch(const uint32_t* keys_in, const uint32_t* vals
   }
   // persistent grid: as many blocks as fit at once (four per SM), or fewer
   // when the capacity needs fewer partitions
-  static int sms[64] = {0};
-  if (dev >= 0 && dev < 64 && sms[dev] == 0) {
-    e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-  }
+  int sms = 0;
+  e = current_sm_count(&sms);
+  if (e != cudaSuccess) return e;
   const int64_t parts = (cap > 0 ? cap + PART - 1 : PART) / PART;
-  const int64_t resident = (dev >= 0 && dev < 64 ? sms[dev] : 152) * 4;
+  const int64_t resident = (int64_t)sms * 4;
   const unsigned grid = (unsigned)(parts < resident ? parts : resident);
   onesweep_kernel<BITS, ITEMS><<<grid, SORT_THREADS, sm, st>>>(
       keys_in, vals_in, keys_out, vals_out, n_dev, n_host, shift, s.hist + (size_t)pass * RADIX,
-      s.lookback + (size_t)pass * s.parts * RADIX, s.part_ctr + pass, reinterpret_cast<uint2*>(ranges), status);
+      s.lookback + (size_t)pass * s.parts * RADIX, s.part_ctr + pass, reinterpret_cast<uint2*>(ranges), status,
+      g_spin_limit, ranges ? g_hold_part : -1);
   return cudaGetLastError();
 }
 
@@ -329,6 +337,11 @@ cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_i
     default: return LS_OS(8, SORT_ITEMS);
   }
 #undef LS_OS
+}
+
+void set_sort_wait(int spin_limit, int hold_part) {
+  g_spin_limit = spin_limit > 0 ? spin_limit : SPIN_LIMIT_DEFAULT;
+  g_hold_part = hold_part;
 }
 
 cudaError_t launch_ranges_fixup(int32_t* ranges, int total_tiles, cudaStream_t st) {

@@ -279,15 +279,17 @@ class Rasterizer:
                                        _stream()), "ls_project_bwd")
         return g
 
-    def render_bwd(self, splats: Splats, cam, state, grad_image, grad_T=None, want_g2d=False):
+    def render_bwd(self, splats: Splats, cam, state, grad_image, grad_T=None, want_g2d=False, out=None):
+        """a5 + a6 in one ls_render_bwd call (the 2D gradient buffer is
+        cleared inside the library); 3D gradients into `out` when given."""
         P = self.params
         n = splats.n
         grad_image = grad_image.contiguous()
         if grad_T is not None:
             grad_T = grad_T.contiguous()
-        g = dict(means=torch.empty_like(splats.means), scales=torch.empty_like(splats.scales),
-                 quats=torch.empty_like(splats.quats), opac=torch.empty_like(splats.opac),
-                 sh=torch.empty_like(splats.sh))
+        g = out or dict(means=torch.empty_like(splats.means), scales=torch.empty_like(splats.scales),
+                        quats=torch.empty_like(splats.quats), opac=torch.empty_like(splats.opac),
+                        sh=torch.empty_like(splats.sh))
         g2d = torch.empty((n, 12), dtype=torch.float32, device=self.device) if want_g2d else None
         wsb = N.lib().ls_render_bwd_workspace(n)
         ws = self._buf("bwd_ws", wsb + 256)

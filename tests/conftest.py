@@ -24,3 +24,18 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """The parity figures the GPU tests measured (image errors, flagged and
+    mismatched pixel fractions, record-field and gradient errors)."""
+    try:
+        from tests.gpu_helpers import PARITY_LOG
+    except Exception:  # pragma: no cover
+        return
+    if not PARITY_LOG:
+        return
+    terminalreporter.write_sep("-", "measured parity")
+    for test, what, fig in PARITY_LOG:
+        vals = " ".join("%s=%.3g" % (k, v) if isinstance(v, float) else "%s=%s" % (k, v) for k, v in fig.items())
+        terminalreporter.write_line("%s %s %s" % (test, what, vals))

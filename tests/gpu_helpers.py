@@ -2,11 +2,22 @@
 comparison rules).  The comparison rules follow the parity bar: tile lists
 and orders bit-exact; images within 1e-4 max abs on pixels the oracle does
 not flag as near a threshold; gradients within 1e-3 relative L2."""
+import os
+
 import numpy as np
 import torch
 
 IMG_TOL = 1e-4
 GRAD_TOL = 1e-3
+
+# Measured parity figures of this session (printed at the end of the run by
+# tests/conftest.py): (test, what, {figure: value}).
+PARITY_LOG = []
+
+
+def log_parity(what, **figures):
+    test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0].split("::")[-1]
+    PARITY_LOG.append((test, what, figures))
 
 
 def pack_records(rec, device="cuda"):
@@ -63,8 +74,12 @@ def assert_image_parity(img, ref, region=None, tol=IMG_TOL, max_flag_frac=0.01):
         refi = ref["image"]
     err = np.abs(img - refi).max(-1)
     ok = ~flags
-    assert err[ok].max() <= tol, "max abs error %.3g on unflagged pixels" % err[ok].max()
     nflag = int(flags.sum())
+    mism = err > tol
+    log_parity("image", pixels=int(flags.size), max_err_unflagged=float(err[ok].max()) if ok.any() else 0.0,
+               flagged_frac=nflag / flags.size, mismatched_frac=float(mism.mean()),
+               max_err_flagged=float(err[flags].max()) if nflag else 0.0)
+    assert err[ok].max() <= tol, "max abs error %.3g on unflagged pixels" % err[ok].max()
     assert nflag <= max(16, max_flag_frac * flags.size), "%d flagged pixels" % nflag
     if nflag:
         assert err[flags].max() <= 2 / 255 + tol

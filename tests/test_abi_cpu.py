@@ -108,3 +108,30 @@ def test_host_argument_checks_reject_before_launch(L):
     # empty problem is valid and launches nothing
     assert L.ls_project(0, None, None, None, None, None, ctypes.byref(cam), 1, ctypes.byref(good.c()), None, None,
                         None, None) == 0
+
+
+def test_noalloc_rejects_bad_cameras_and_tiles_before_any_arithmetic(L):
+    """ls_duplicate_sort_noalloc applies ls_duplicate_sort's own camera and
+    parameter rules before it counts tiles: a width near INT_MAX or a tile
+    shape outside {8x8, 16x16, 32x16} is an invalid argument, not an
+    overflow."""
+    from paper_2411_12440_gb300 import raster, scenes
+    fake = ctypes.c_void_p(16)
+    good = raster.RenderParams()
+    huge = raster.cam_array([dict(scenes.identity_camera(64, 64), width=2 ** 31 - 1)])
+    assert L.ls_duplicate_sort_noalloc(10, fake, huge, 1, ctypes.byref(good.c()), 100, fake, fake, fake, fake, None,
+                                       None) == 1
+    cam = raster.cam_array([scenes.identity_camera(64, 64)])
+    odd = raster.RenderParams(tile_w=12, tile_h=12)
+    assert L.ls_duplicate_sort_noalloc(10, fake, cam, 1, ctypes.byref(odd.c()), 100, fake, fake, fake, fake, None,
+                                       None) == 1
+    # beyond the static scratch: unsupported, still before any launch
+    assert L.ls_duplicate_sort_noalloc(70_000, fake, cam, 1, ctypes.byref(good.c()), 100, fake, fake, fake, fake,
+                                       None, None) == 5
+
+
+def test_debug_sort_wait_setter_checks_arguments(L):
+    assert L.ls_debug_set_sort_wait(-1, -1) == 1
+    assert L.ls_debug_set_sort_wait(0, -2) == 1
+    assert L.ls_debug_set_sort_wait(1000, 0) == 0
+    assert L.ls_debug_set_sort_wait(0, -1) == 0  # defaults again

@@ -589,3 +589,27 @@ def test_reach_lists_between_touched_pairs_and_boxes(tw, th):
     # tight: boxes of one or two tiles are taken whole and the test is against
     # the rectangle of pixel centres, yet the lists stay near the pixel-exact set
     assert len(k) < 1.25 * len(t)
+
+
+def test_tile_mask_sample_equals_full_render_on_its_tiles():
+    """The timing sample of the CPU baseline composites a subset of tiles: on
+    those tiles it is the full render bit for bit (image, T and adjoint
+    terms), and it leaves the other tiles untouched."""
+    s, cams, _ = scenes.make_workload("plain_10k_256", n=1200)
+    cam = cams[0]
+    W, H = cam["width"], cam["height"]
+    P = dict(bg=(0.2, 0.3, 0.1))
+    proj, vis = oracle.project(s, cam, P)
+    tiles = (W // 16) * (H // 16)
+    mask = np.random.default_rng(3).random(tiles) < 0.25
+    full = oracle.render(proj, vis, W, H, P)
+    part = oracle.render(proj, vis, W, H, P, tile_mask=mask)
+    pix = np.repeat(np.repeat(mask.reshape(H // 16, W // 16), 16, 0), 16, 1)
+    assert np.array_equal(part["image"][pix], full["image"][pix])
+    assert np.array_equal(part["T"][pix], full["T"][pix])
+    assert not part["image"][~pix].any() and not part["T"][~pix].any()
+    gC = np.random.default_rng(4).standard_normal((H, W, 3))
+    gT = np.random.default_rng(5).standard_normal((H, W))
+    g_part = oracle.render_bwd(proj, vis, W, H, gC, gT, P, tile_mask=mask)
+    g_win = oracle.render_bwd(proj, vis, W, H, gC * pix[..., None], gT * pix, P)
+    assert np.allclose(g_part, g_win, rtol=1e-12, atol=1e-12)
