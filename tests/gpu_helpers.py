@@ -57,12 +57,14 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-def assert_image_parity(img, ref, region=None, tol=IMG_TOL, max_flag_frac=0.01):
-    """img (GPU, float32) against the oracle output dict: max abs error on
-    unflagged pixels <= tol; flagged pixels (a pair within 1e-5 of alpha_min,
-    T within 1e-9 of T_min, or alpha within 1e-6 of the clamp) are at most
-    max_flag_frac of the region (their count grows with the pairs per pixel
-    and with flat kernel tails) and each within 2/255 + tol."""
+def assert_image_parity(img, ref, region=None, tol=IMG_TOL, max_mismatch_frac=1e-4):
+    """img (GPU, float32) against the oracle output dict: max abs error
+    <= tol on pixels the oracle does not flag; the pixels beyond tol (a
+    skip/stop decision that binary32 and FP64 took differently: a pair
+    within 1e-5 of alpha_min, T within 1e-9 of T_min, alpha within 1e-6 of
+    the clamp) must all be flagged ones, at most max_mismatch_frac of the
+    region (at least one pixel allowed), each within 1/255 + tol (one pair
+    of alpha ~ alpha_min added or dropped)."""
     img = np.asarray(img, np.float64)
     flags = ref["flags"]
     if region is not None:
@@ -80,9 +82,9 @@ def assert_image_parity(img, ref, region=None, tol=IMG_TOL, max_flag_frac=0.01):
                flagged_frac=nflag / flags.size, mismatched_frac=float(mism.mean()),
                max_err_flagged=float(err[flags].max()) if nflag else 0.0)
     assert err[ok].max() <= tol, "max abs error %.3g on unflagged pixels" % err[ok].max()
-    assert nflag <= max(16, max_flag_frac * flags.size), "%d flagged pixels" % nflag
-    if nflag:
-        assert err[flags].max() <= 2 / 255 + tol
+    assert int(mism.sum()) <= max(1, max_mismatch_frac * flags.size), "%d pixels beyond tol" % int(mism.sum())
+    if mism.any():
+        assert err[mism].max() <= 1 / 255 + tol, err[mism].max()
     return float(err[ok].max()), nflag
 
 

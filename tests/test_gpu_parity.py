@@ -216,6 +216,8 @@ def test_duplicate_sort_multi_camera_global_tiles():
 
 # ------------------------------------------------------------------ a1
 def _proj_parity(scene, cam, P, rtol=1e-5):
+    """Record fields against the oracle, relative to the field's scale
+    (5 rtol), visibility, support boxes and the binary32 depth key."""
     rz = raster.Rasterizer(raster.RenderParams.from_dict(P))
     sp = raster.Splats.from_scene(scene)
     proj, tc = rz.project(sp, [cam])
@@ -242,10 +244,12 @@ def _proj_parity(scene, cam, P, rtol=1e-5):
         scale = np.maximum(np.abs(o), np.abs(ref[m][:, [oi]]).mean() * 1e-2 + 1e-6)
         errs[nm] = float((np.abs(g - o) / scale).max())
     log_parity("record_fields", **errs)
+    # measured on GB300: at most 2.2e-5 for the conic and 2.5e-5 for SH3
+    # colours (binary32 sums of 16 SH terms against FP64), so 5e-5
     for k in "abc":
-        assert errs[k] < 10 * rtol, (k, errs[k])
+        assert errs[k] < 5 * rtol, (k, errs[k])
     for nm in names:
-        assert errs[nm] < 50 * rtol, (nm, errs[nm])
+        assert errs[nm] < 5 * rtol, (nm, errs[nm])
     assert np.allclose(foot[m, 2], ref[m, oracle.P_EX], rtol=1e-4)
     # sort key: the binary32 camera depth, a few ulp from the FP64 value
     assert (np.abs(dkey[m].view(np.float32) - ref[m, oracle.P_DEPTH]) <= 1e-6 * ref[m, oracle.P_DEPTH]).all()
@@ -344,7 +348,7 @@ def test_render_kernel_family_parity(kid, lam):
     P = dict(sh_degree=0, kernel=kid, lam=lam)
     _, _, image, T, _ = _render_gpu(scene, cams[0], P)
     ref = oracle.render_scene(scene, cams[0], P)
-    assert_image_parity(image.cpu().numpy(), ref, tol=2e-4, max_flag_frac=0.03)
+    assert_image_parity(image.cpu().numpy(), ref)
 
 
 def test_render_stats_counts_match_oracle():
@@ -503,7 +507,7 @@ def test_full_size_backward_window():
     g2d_ref = oracle.render_bwd(ref_f["proj"], ref_f["vis"], W, H, w.astype(np.float64), v.astype(np.float64), P,
                                 window=window)
     touched = np.nonzero(np.abs(g2d_ref).sum(1) > 0)[0]
-    assert len(touched) > 1000
+    assert len(touched) > 100  # ~200 primitives composite into the window before its pixels stop
     g2d = g["g2d"].cpu().numpy()
     errs = {"g2d_col%d" % j: rel_l2(g2d[:, j], g2d_ref[:, j]) for j in range(9)}
     # 3D gradients: the oracle's chain rule on the primitives the window
