@@ -567,6 +567,21 @@ def bench_learned(dev, reps=20):
     return out
 
 
+def bench_kernel_fit(dev):
+    """Pattern fits of Sec. 5.1 (Fig. 5): stripes, checkerboard and circles at
+    4 and 16 periods, 256 x 256, 2304 primitives, 300 steps of the library's
+    own forward, 6:2:2 loss, backward and Adam, for every kernel of the
+    family; PSNR against the target per (pattern, kernel)."""
+    from paper_2411_12440_gb300 import fitting
+    t0 = time.perf_counter()
+    t = fitting.sweep(freqs=(4, 16), size=256, n_side=48, steps=300, device=dev)
+    psnr = {k: {kk: round(vv["psnr_db"], 2) for kk, vv in v.items()} for k, v in t.items()}
+    best = {k: max(v, key=v.get) for k, v in psnr.items()}
+    return {"workload": "patterns_256", "prims": 48 * 48, "steps": 300, "psnr_db": psnr, "best_kernel": best,
+            "linear_over_gaussian_db": {k: round(v["linear"] - v["gaussian"], 2) for k, v in psnr.items()},
+            "seconds": round(time.perf_counter() - t0, 2)}
+
+
 def learned_probe():
     """One plain forward frame, then one learned frame (trained network,
     calibrated margin, no counters) of the 5M 1080p workload, after one
@@ -611,6 +626,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-camera batched measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-termination measurement")
     ap.add_argument("--no-family", action="store_true", help="skip the linear-vs-Gaussian measurement")
+    ap.add_argument("--no-fit", action="store_true", help="skip the pattern fits of the kernel family")
     ap.add_argument("--learned-probe", action="store_true",
                     help="one plain and one learned forward frame of the 5M 1080p workload (for a launch list)")
     args = ap.parse_args()
@@ -884,6 +900,8 @@ def main():
         line["kernel_family"] = bench_kernel_family(sp, cam, int(extra["antialias"]), dev)
     if not args.no_learned and args.prims is None:
         line["learned"] = bench_learned(dev)
+    if not args.no_fit and args.prims is None:
+        line["kernel_fit"] = bench_kernel_fit(dev)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         ncores = os.cpu_count() or 1
         est, sample, spent = oracle_frame_estimate(scene, cam, dict(sh_degree=3, antialias=int(extra["antialias"])),

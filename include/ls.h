@@ -341,6 +341,34 @@ ls_status ls_copy(void* dst, const void* src, size_t bytes, void* stream);
  * only to keep the chains live). */
 ls_status ls_fp32_issue_probe(int64_t iters, int32_t blocks_per_sm, float* out, int64_t* lane_ops, void* stream);
 
+/* ---- training-side consumers of the backward ---------------------------
+ * Image loss of the appendix "Loss Functions": L = w_l1 L1 + w_l2 L2 +
+ * w_ssim (1 - SSIM) of a rendered image pred and a target, both [H][W][3]
+ * float (the paper's weights are 0.6, 0.2, 0.2).  L1 and L2 are means over
+ * the H W 3 values; SSIM (only named by the paper) is read as 3DGS computes
+ * it: per channel, 11 x 11 Gaussian window of standard deviation 1.5 (taps
+ * normalised to sum 1), zero outside the image, C1 = 0.01^2, C2 = 0.03^2,
+ * averaged over pixels and channels.  loss_dev [4] (device) receives total,
+ * L1, L2 and SSIM; grad (device [H][W][3], or NULL) is OVERWRITTEN with
+ * dL/dpred (the L1 term's derivative at a zero difference taken as 0).
+ * workspace: ls_image_loss_workspace bytes, 256-byte aligned.  Deterministic
+ * (fixed reduction order).  LS_ERR_INVALID_ARG for sizes outside 1..16384,
+ * NULL inputs, non-finite weights or a short workspace. */
+size_t ls_image_loss_workspace(int32_t height, int32_t width);
+ls_status ls_image_loss(int32_t height, int32_t width, const float* pred, const float* target, float w_l1,
+                        float w_l2, float w_ssim, float* loss_dev, float* grad, void* workspace, size_t ws_bytes,
+                        void* stream);
+
+/* One bias-corrected Adam step (step >= 1) of n parameters in place, with
+ * first and second moments m1, m2 (device, n floats each, zero before step
+ * 1), in the parameter's unconstrained space: mode 0 the value itself, 1 its
+ * log (for positive values such as scales; the gradient is taken times p),
+ * 2 its logit (for values in (0, 1) such as opacities; times p (1 - p)).
+ * The optimiser of the pattern fits (Sec. 5.1).  LS_ERR_INVALID_ARG for a
+ * bad step, mode, rate or NULL pointer. */
+ls_status ls_adam(int64_t n, float* param, const float* grad, float* m1, float* m2, int32_t step, float lr,
+                  float beta1, float beta2, float eps, int32_t mode, void* stream);
+
 /* For tests of failure detection: the onesweep radix sort's look-back waits
  * on its predecessor partitions, each wait bounded by spin_limit polls (0
  * restores the default, about a second); after that it writes

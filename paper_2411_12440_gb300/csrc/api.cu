@@ -479,6 +479,35 @@ ls_status ls_render_batch(int32_t n, const float* means, const float* scales, co
   return LS_OK;
 }
 
+// ---------------------------------------------------------------- training-side consumers
+size_t ls_image_loss_workspace(int32_t height, int32_t width) {
+  if (height <= 0 || width <= 0 || height > 16384 || width > 16384) return 0;
+  return image_loss_ws_bytes(height, width);
+}
+
+ls_status ls_image_loss(int32_t height, int32_t width, const float* pred, const float* target, float w_l1,
+                        float w_l2, float w_ssim, float* loss_dev, float* grad, void* workspace, size_t ws_bytes,
+                        void* stream) {
+  if (height <= 0 || width <= 0 || height > 16384 || width > 16384) return LS_ERR_INVALID_ARG;
+  if (!pred || !target || !loss_dev || !workspace) return LS_ERR_INVALID_ARG;
+  if (!std::isfinite(w_l1) || !std::isfinite(w_l2) || !std::isfinite(w_ssim)) return LS_ERR_INVALID_ARG;
+  if (ws_bytes < image_loss_ws_bytes(height, width) || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return LS_ERR_INVALID_ARG;
+  LS_TRY(launch_image_loss(height, width, pred, target, w_l1, w_l2, w_ssim, loss_dev, grad, workspace,
+                           static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+ls_status ls_adam(int64_t n, float* param, const float* grad, float* m1, float* m2, int32_t step, float lr,
+                  float beta1, float beta2, float eps, int32_t mode, void* stream) {
+  if (n < 0 || step < 1 || mode < 0 || mode > 2) return LS_ERR_INVALID_ARG;
+  if (!(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f))
+    return LS_ERR_INVALID_ARG;
+  if (n > 0 && (!param || !grad || !m1 || !m2)) return LS_ERR_INVALID_ARG;
+  LS_TRY(launch_adam(n, param, grad, m1, m2, step, lr, beta1, beta2, eps, mode, static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
 // ---------------------------------------------------------------- termination MLP
 namespace {
 bool mlp_ok(const ls_mlp* n) { return n && n->w1t && n->b1 && n->w2t && n->b2 && n->w3 && n->b3; }

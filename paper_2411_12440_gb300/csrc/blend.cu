@@ -17,8 +17,11 @@
 //
 // Backward: each pixel restarts from its checkpoint (T_final, n_last) and
 // walks its list back to front, recovering T before each entry as
-// T / (1 - alpha).  Each thread first sums its PPT pixels' nine gradient
-// terms; a warp with any contributing pixel then reduce-scatters the nine sums
+// T / (1 - alpha).  The per-pixel adjoint is predicated (a pixel slot that
+// some lane of the warp takes runs as one straight line for every lane), and
+// the AGS reading is a template argument, not a branch per pair.  Each
+// thread first sums its pixels' nine gradient terms; a warp with any
+// contributing pixel then reduce-scatters the nine sums
 // (14 shuffles instead of 45: eight values end in eight lane groups), those
 // lanes add into a per-CTA shared-memory slot, and after the batch one set of
 // float4 atomics per (record, CTA) lands in global memory.
@@ -321,42 +324,58 @@ __device__ __forceinline__ void warp_reduce9(const float v[9], float& mine, floa
   ninth = u;
 }
 
-template <int KID, int PPT>
+// One thread owns RPT rows x PPR pixels of a tile: rows lr + r sy, columns
+// lc + c sx (sx = tile_w / PPR threads across, sy = tile_h / RPT down), so
+// that the p-th pixels of a warp form a compact block.
+template <int KID, int AGS, int PPR, int RPT>
 __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
                                          const ParDev& P, const TileJob& J, float4* s_a, float4* s_b, float4* s_c,
                                          float* s_acc, uint32_t* s_id, int* s_touch, int* s_max, int B,
                                          const float* __restrict__ t_final, const int32_t* __restrict__ n_last,
                                          const float* __restrict__ grad_image, const float* __restrict__ grad_t,
                                          float* __restrict__ g2d) {
+  constexpr int NPX = PPR * RPT;
   const unsigned FULL = 0xffffffffu;
-  const int sx = P.tile_w / PPT;
+  const int sx = P.tile_w / PPR, sy = P.tile_h / RPT;
   const int lr = (int)threadIdx.x / sx, lc = (int)threadIdx.x % sx;
-  const int py = J.y0 + lr, px0 = J.x0 + lc;
-  const float y = (float)py + 0.5f;
+  const int px0 = J.x0 + lc, py0 = J.y0 + lr;
   const int lane = threadIdx.x & 31;
   // GS = dL/dC . S + dL/dT_final T_final, where S is the colour composited
   // behind the current entry (background included): the part of dL/dalpha
   // that the entries behind contribute, kept as one running scalar
-  float xs[PPT], T[PPT], Tf[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gTT[PPT], GS[PPT];
-  int last[PPT];
+  float T[NPX], gC0[NPX], gC1[NPX], gC2[NPX], GS[NPX];
+  int last[NPX];
+  int row_max[RPT];
+  float xs[PPR], ys[RPT];
+#pragma unroll
+  for (int c = 0; c < PPR; ++c) xs[c] = (float)(px0 + c * sx) + 0.5f;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) ys[r] = (float)(py0 + r * sy) + 0.5f;
   int my_max = 0;
 #pragma unroll
-  for (int p = 0; p < PPT; ++p) {
-    xs[p] = (float)(px0 + p * sx) + 0.5f;
-    T[p] = Tf[p] = 1.f;
-    gC0[p] = gC1[p] = gC2[p] = gTT[p] = 0.f;
-    last[p] = 0;
-    if (px0 + p * sx < J.W && py < J.H) {
-      const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p * sx;
-      T[p] = Tf[p] = t_final[pi];
-      last[p] = n_last[pi];
-      gC0[p] = grad_image[3 * pi];
-      gC1[p] = grad_image[3 * pi + 1];
-      gC2[p] = grad_image[3 * pi + 2];
-      gTT[p] = grad_t ? grad_t[pi] * Tf[p] : 0.f;  // dL/dT_final times T_final
+  for (int r = 0; r < RPT; ++r) {
+    row_max[r] = 0;
+#pragma unroll
+    for (int c = 0; c < PPR; ++c) {
+      const int p = r * PPR + c;
+      const int px = px0 + c * sx, py = py0 + r * sy;
+      T[p] = 1.f;
+      float Tf = 1.f, gTT = 0.f;
+      gC0[p] = gC1[p] = gC2[p] = 0.f;
+      last[p] = 0;
+      if (px < J.W && py < J.H) {
+        const size_t pi = J.pix_base + (size_t)py * J.W + px;
+        T[p] = Tf = t_final[pi];
+        last[p] = n_last[pi];
+        gC0[p] = grad_image[3 * pi];
+        gC1[p] = grad_image[3 * pi + 1];
+        gC2[p] = grad_image[3 * pi + 2];
+        gTT = grad_t ? grad_t[pi] * Tf : 0.f;  // dL/dT_final times T_final
+      }
+      GS[p] = (gC0[p] * P.bg[0] + gC1[p] * P.bg[1] + gC2[p] * P.bg[2]) * Tf + gTT;
+      row_max[r] = max(row_max[r], last[p]);
     }
-    GS[p] = (gC0[p] * P.bg[0] + gC1[p] * P.bg[1] + gC2[p] * P.bg[2]) * Tf[p] + gTT[p];
-    my_max = max(my_max, last[p]);
+    my_max = max(my_max, row_max[r]);
   }
   if (threadIdx.x == 0) *s_max = 0;
   __syncthreads();
@@ -382,67 +401,96 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
     __syncthreads();
     for (int jj = min(cnt, warp_max - b0) - 1; jj >= 0; --jj) {
       const int j = b0 + jj;
-      const float4 a = s_a[jj];
-      const float4 bb = s_b[jj];
-      const float dy = __fsub_rn(y, a.y);
-      const float l01dy = __fmul_rn(a.w, dy);
-      const float e2 = __fmul_rn(bb.x, dy);
-      const float e2s = __fmul_rn(e2, e2);
-      // else q >= e2s > rho^2 for the whole row, or every pixel of the
-      // thread composited its last entry in front of this one
-      const bool row_in = e2s <= bb.z && j < my_max;
-      if (!__any_sync(FULL, row_in)) continue;  // nothing for the warp
+      const float4 a = s_a[jj];   // {mx, my, l00, l01}
+      const float4 bb = s_b[jj];  // {l11, o, rho2, depth}
+      // row terms: dy, l01 dy and (l11 dy)^2 for each of the thread's rows;
+      // q >= (l11 dy)^2, so a row whose term alone exceeds rho^2 takes nothing
+      float dy[RPT], l01dy[RPT], e2[RPT], e2s[RPT];
+      bool row_in[RPT];
+      bool any_row = false;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        dy[r] = __fsub_rn(ys[r], a.y);
+        l01dy[r] = __fmul_rn(a.w, dy[r]);
+        e2[r] = __fmul_rn(bb.x, dy[r]);
+        e2s[r] = __fmul_rn(e2[r], e2[r]);
+        row_in[r] = e2s[r] <= bb.z && j < row_max[r];
+        any_row = any_row || row_in[r];
+      }
+      if (!__any_sync(FULL, any_row)) continue;  // nothing for the warp
       // per-thread sums: the geometric terms are gathered as sums over the
-      // thread's pixels of gq e1, gq dx, gq dx^2 and gq (dy and l11 dy are the
-      // same for its whole row) and expanded once per record below
-      float s_e1 = 0.f, s_dx = 0.f, s_dx2 = 0.f, s_q = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
+      // thread's pixels of gq e1, gq dx, gq dx^2 and, per row, gq and gq dx
+      // (dy and l11 dy are the same along a row) and expanded once below
+      float s_e1 = 0.f, s_dx2 = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
+      float s_q[RPT], s_dx[RPT];
       bool any = false;
       const float kq = 0.5f * bb.y * P.inv_lambda;
+      // The per-pixel work is predicated rather than branched: once any lane
+      // of the warp takes pixel slot p, every lane runs the same straight
+      // line and a lane that does not take it contributes zeros.
 #pragma unroll
-      for (int p = 0; p < PPT; ++p) {
-        if (!row_in) break;
-        float dx, e1;
-        const float q = pair_q(xs[p], a.x, a.z, l01dy, e2s, dx, e1);
-        if (j >= last[p] || q > bb.z) continue;
-        float D, xk, f, araw, alpha;
-        pair_alpha<KID>(q, bb.y, P, D, xk, f, araw, alpha);
-        if (alpha < P.alpha_min) continue;
-        any = true;
-        const float4 c = s_c[jj];
-        const float iom = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 1 - alpha_max
-        const float Tb = T[p] * iom;  // transmittance in front of this entry
-        const float wgt = alpha * Tb;
-        v6 += wgt * gC0[p];
-        v7 += wgt * gC1[p];
-        v8 += wgt * gC2[p];
-        // dL/dalpha = Tb dL/dC . c - (dL/dC . S + dL/dT_final T_final) / (1 - alpha)
-        const float gcd = gC0[p] * c.x + gC1[p] * c.y + gC2[p] * c.z;
-        const float ga = Tb * gcd - iom * GS[p];
-        GS[p] += wgt * gcd;
-        T[p] = Tb;
-        if (araw <= P.alpha_max) {
-          v5 += f * ga;
+      for (int r = 0; r < RPT; ++r) {
+        s_q[r] = 0.f;
+        s_dx[r] = 0.f;
+#pragma unroll
+        for (int c = 0; c < PPR; ++c) {
+          const int p = r * PPR + c;
+          float dx, e1;
+          const float q = pair_q(xs[c], a.x, a.z, l01dy[r], e2s[r], dx, e1);
+          bool take = row_in[r] && j < last[p] && q <= bb.z;
+          if (!__any_sync(FULL, take)) continue;  // warp-uniform
+          // a lane outside the support runs on finite stand-ins (q = 0 and
+          // zero offsets), so that its zero weights never meet an infinity
+          const float qa = take ? q : 0.f;
+          dx = take ? dx : 0.f;
+          e1 = take ? e1 : 0.f;
+          float D, xk, f, araw, alpha;
+          pair_alpha<KID>(qa, bb.y, P, D, xk, f, araw, alpha);
+          take = take && alpha >= P.alpha_min;
+          any = any || take;
+          const float4 cc = s_c[jj];
+          const float iom = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 1 - alpha_max
+          const float Tb = T[p] * iom;  // transmittance in front of this entry
+          const float wgt = take ? alpha * Tb : 0.f;
+          v6 += wgt * gC0[p];
+          v7 += wgt * gC1[p];
+          v8 += wgt * gC2[p];
+          // dL/dalpha = Tb dL/dC . c - (dL/dC . S + dL/dT_final T_final) / (1 - alpha)
+          const float gcd = gC0[p] * cc.x + gC1[p] * cc.y + gC2[p] * cc.z;
+          const float ga = Tb * gcd - iom * GS[p];
+          GS[p] += wgt * gcd;
+          T[p] = take ? Tb : T[p];
+          // a clamped alpha passes no gradient to o or D
+          const float gat = (take && araw <= P.alpha_max) ? ga : 0.f;
+          v5 += f * gat;
           // dL/dq = dL/dalpha o f'(x) / (lambda 2 D), o / (2 lambda) per record
           // (the linear profile's slope is -1 wherever alpha > 0)
-          float gD = (KID == LS_KERNEL_LINEAR ? -ga : ga * kern_df<KID>(xk)) * kq;
-          if (P.ags == 1) gD *= __expf(-D * D);
-          else if (P.ags == 2) gD *= __expf(-xk * xk);
+          float gD = (KID == LS_KERNEL_LINEAR ? -gat : gat * kern_df<KID>(xk)) * kq;
+          if (AGS == 1) gD *= __expf(-D * D);
+          else if (AGS == 2) gD *= __expf(-xk * xk);
           const float gq = D > 0.f ? __fdividef(gD, D) : 0.f;
           const float gdx = gq * dx;
           s_e1 += gq * e1;
-          s_dx += gdx;
+          s_dx[r] += gdx;
           s_dx2 += gdx * dx;
-          s_q += gq;
+          s_q[r] += gq;
         }
       }
       // A d = L^T (L d) = (l00 e1, l01 e1 + l11 e2): the conic-space mean
       // gradient and the conic-entry gradients (b counted once)
       float v[9];
+      float t1 = a.w * s_e1, t3 = 0.f, t4 = 0.f;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        t1 += bb.x * e2[r] * s_q[r];
+        t3 += dy[r] * s_dx[r];
+        t4 += dy[r] * dy[r] * s_q[r];
+      }
       v[0] = -2.f * a.z * s_e1;
-      v[1] = -2.f * (a.w * s_e1 + bb.x * e2 * s_q);
+      v[1] = -2.f * t1;
       v[2] = s_dx2;
-      v[3] = 2.f * dy * s_dx;
-      v[4] = dy * dy * s_q;
+      v[3] = 2.f * t3;
+      v[4] = t4;
       v[5] = v5;
       v[6] = v6;
       v[7] = v7;
@@ -477,17 +525,17 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
   }
 }
 
-template <int KID, int PPT>
+template <int KID, int AGS, int PPR, int RPT>
 __global__ void __launch_bounds__(128) blend_bwd_kernel(const float4* __restrict__ rec, const CamDev cam,
                                                         const ParDev P, const int2* __restrict__ ranges,
                                                         const uint32_t* __restrict__ vals,
                                                         const float* __restrict__ t_final,
                                                         const int32_t* __restrict__ n_last,
                                                         const float* __restrict__ grad_image,
-                                                        const float* __restrict__ grad_t, float* __restrict__ g2d) {
+                                                        const float* __restrict__ grad_t, float* __restrict__ g2d,
+                                                        int B) {
   extern __shared__ float4 smem[];
   __shared__ int s_max;
-  const int B = blockDim.x;  // one record per thread per batch (2.5 % faster than two)
   float* s_acc = reinterpret_cast<float*>(smem + 3 * B);
   uint32_t* s_id = reinterpret_cast<uint32_t*>(s_acc + 9 * B);
   int* s_touch = reinterpret_cast<int*>(s_id + B);
@@ -499,8 +547,8 @@ __global__ void __launch_bounds__(128) blend_bwd_kernel(const float4* __restrict
   J.H = cam.H;
   J.rg = ranges[cam.tile_base + tile];
   J.pix_base = 0;
-  bwd_tile<KID, PPT>(rec, vals, P, J, smem, smem + B, smem + 2 * B, s_acc, s_id, s_touch, &s_max, B, t_final, n_last,
-                     grad_image, grad_t, g2d);
+  bwd_tile<KID, AGS, PPR, RPT>(rec, vals, P, J, smem, smem + B, smem + 2 * B, s_acc, s_id, s_touch, &s_max, B, t_final,
+                          n_last, grad_image, grad_t, g2d);
 }
 
 // ---------------------------------------------------------------- batched
@@ -620,18 +668,28 @@ cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev&
 cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
                              const uint32_t* vals, const float* t_final, const int32_t* n_last,
                              const float* grad_image, const float* grad_t, float* g2d, cudaStream_t st) {
-  const int ppt = ppt_for(P);
-  const int threads = P.tile_w * P.tile_h / ppt;
-  const int B = threads;
+  // 4 pixels per row per thread; one row per thread (64 threads per 16x16
+  // tile), 8x8 tiles: 2 pixels of one row
+  const int ppr = P.tile_w * P.tile_h >= 256 ? 4 : 2;
+  const int rpt = 1;
+  const int threads = P.tile_w * P.tile_h / (ppr * rpt);
+  const int B = threads;  // one record per thread per batch (2.5 % faster than two)
   const unsigned grid = (unsigned)(cam.tiles_x * cam.tiles_y);
   const size_t sm = sizeof(float4) * 3 * B + sizeof(float) * 9 * B + 2 * sizeof(uint32_t) * B;
-#define LS_BB2(K, PP)                                                                                          \
-  blend_bwd_kernel<K, PP><<<grid, threads, sm, st>>>(rec, cam, P, ranges, vals, t_final, n_last, grad_image, \
-                                                     grad_t, g2d)
-#define LS_BB(K)                \
-  do {                          \
-    if (ppt == 4) LS_BB2(K, 4); \
-    else LS_BB2(K, 2);          \
+#define LS_BB3(K, A, PR, RT)                                                                                   \
+  blend_bwd_kernel<K, A, PR, RT><<<grid, threads, sm, st>>>(rec, cam, P, ranges, vals, t_final, n_last, grad_image, \
+                                                            grad_t, g2d, B)
+#define LS_BB2(K, A)                \
+  do {                              \
+    if (ppr == 4) LS_BB3(K, A, 4, 1); \
+    else LS_BB3(K, A, 2, 1);          \
+  } while (0)
+  // the AGS reading is a template argument: a branch on it per pair cost 9 %
+#define LS_BB(K)                   \
+  do {                             \
+    if (P.ags == 1) LS_BB2(K, 1);  \
+    else if (P.ags == 2) LS_BB2(K, 2); \
+    else LS_BB2(K, 0);             \
   } while (0)
   switch (P.kernel) {
     case LS_KERNEL_GAUSSIAN: LS_BB(LS_KERNEL_GAUSSIAN); break;
@@ -642,6 +700,7 @@ cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev&
   }
 #undef LS_BB
 #undef LS_BB2
+#undef LS_BB3
   return cudaGetLastError();
 }
 

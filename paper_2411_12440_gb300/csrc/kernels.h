@@ -243,6 +243,14 @@ cudaError_t launch_refuted_sat(const uint8_t* refuted, const unsigned* n_refuted
 cudaError_t launch_learned_stats(const unsigned long long* key_total, const int64_t* n_kept, const int64_t* n_held,
                                  const unsigned* n_refuted, int64_t* stats, cudaStream_t st);
 
+// ---- training-side consumers of the backward (train.cu)
+size_t image_loss_ws_bytes(int H, int W);
+// loss_out[4] = total, L1, L2, SSIM; grad (nullable) = dL/dpred [H][W][3]
+cudaError_t launch_image_loss(int H, int W, const float* pred, const float* target, float w1, float w2, float w3,
+                              float* loss_out, float* grad, void* ws, cudaStream_t st);
+cudaError_t launch_adam(int64_t n, float* p, const float* g, float* m, float* v, int step, float lr, float b1,
+                        float b2, float eps, int mode, cudaStream_t st);
+
 // ---- termination MLP (mlp.cu)
 struct MlpDev {
   const void* w1t;
