@@ -369,6 +369,69 @@ ls_status ls_image_loss(int32_t height, int32_t width, const float* pred, const 
 ls_status ls_adam(int64_t n, float* param, const float* grad, float* m1, float* m2, int32_t step, float lr,
                   float beta1, float beta2, float eps, int32_t mode, void* stream);
 
+/* Densification statistics, the thresholds of the appendix's densification
+ * table (3DLS row in brackets).  The paper builds on gsplat v1.3 and gives
+ * only the six values; they are read as that library's default strategy
+ * applies them:
+ *   ls_densify_accumulate, after each backward of one view: every primitive
+ *   whose support box meets the image adds the norm of its screen-mean
+ *   gradient in normalised device units, |(g_mx W/2 n_cams, g_my H/2
+ *   n_cams)|, to grad_accum [n], adds 1 to count [n] and raises max_radius
+ *   [n] to max(ex, ey) / max(W, H).  g2d [n][12] as ls_render_bwd's g2d_out
+ *   (g_mx, g_my first), proj the view's records (n_cams = 1 at projection;
+ *   n_cams here is the number of views averaged into one step's loss).
+ *   ACCUMULATED (zero the three arrays at a refinement step).
+ *   ls_densify_decide, at a refinement step, with g = grad_accum / max(count,
+ *   1) and s = the largest of a primitive's three scales: flags [n] (uint8)
+ *   bit 0 duplicate (g > grad2d and s <= grow_scale3d * extent), bit 1 split
+ *   (g > grad2d and s above it, or max_radius > grow_scale2d when
+ *   use_scale2d), bit 2 prune (opacity < prune_opacity, or s >
+ *   prune_scale3d * extent when use_prune_scale3d, or max_radius >
+ *   prune_scale2d when use_scale2d); counts_dev [3] (int64, device, or NULL)
+ *   receives how many primitives carry each bit.  Binary32, every operation
+ *   rounded once (decisions reproducible bit for bit). */
+typedef struct {
+  float grad2d;              /* [0.0002] */
+  float grow_scale2d;        /* [0.05] */
+  float grow_scale3d;        /* times the scene extent [0.006] */
+  float prune_scale2d;       /* [0.15] */
+  float prune_scale3d;       /* times the scene extent [0.4] */
+  float prune_opacity;       /* [0.025] */
+  int32_t use_scale2d;       /* the two 2D-radius rules [0] */
+  int32_t use_prune_scale3d; /* the 3D-scale prune [0] */
+} ls_densify_params;
+ls_status ls_densify_accumulate(int32_t n, const float* g2d, const void* proj, const ls_camera* cam, int32_t n_cams,
+                                float* grad_accum, int32_t* count, float* max_radius, void* stream);
+ls_status ls_densify_decide(int32_t n, const float* grad_accum, const int32_t* count, const float* max_radius,
+                            const float* scales, const float* opacities, float scene_extent,
+                            const ls_densify_params* params, uint8_t* flags, int64_t* counts_dev, void* stream);
+
+/* ---- 3D smoothing filter of the anti-aliased variant ---------------------
+ * Sec. 4.1 evaluates 3DLS+AA with the anti-aliasing of Mip-Splatting; its
+ * 2D filter is ls_params.antialias.  Its 3D filter, read (the paper gives no
+ * formula): each primitive's highest sampling rate over the training cameras
+ * that see its centre, nu = max fx / z (camera depth z > near_plane, the
+ * projected centre within 1.15x the image: x in [-0.15 W, 1.15 W], y in
+ * [-0.15 H, 1.15 H]), bounds its frequency; the variance v = s2 / nu^2
+ * (s2 = 0.2 in Mip-Splatting) is added to all three axes.
+ *   ls_filter3d_variance: filter_var [n] from means [n][3] and the cameras
+ *     (host array, 1..LS_MAX_CAMS); a primitive no camera sees takes the
+ *     largest v of the others (0 when none is seen).  workspace:
+ *     ls_filter3d_workspace() bytes of device scratch, 256-byte aligned.
+ *   ls_filter3d_apply: scales_out = sqrt(scales^2 + v) per axis and
+ *     opacities_out = o prod_k scales_k / scales_out_k (keeps o sqrt(det
+ *     Sigma)); feed them to ls_project.
+ *   ls_filter3d_apply_bwd: gradients with respect to the unfiltered scales
+ *     and opacities from those of the filtered ones (OVERWRITTEN). */
+size_t ls_filter3d_workspace(void);
+ls_status ls_filter3d_variance(int32_t n, const float* means, const ls_camera* cams, int32_t n_cams, float near_plane,
+                               float s2, float* filter_var, void* workspace, size_t ws_bytes, void* stream);
+ls_status ls_filter3d_apply(int32_t n, const float* scales, const float* opacities, const float* filter_var,
+                            float* scales_out, float* opacities_out, void* stream);
+ls_status ls_filter3d_apply_bwd(int32_t n, const float* scales, const float* opacities, const float* filter_var,
+                                const float* g_scales_out, const float* g_opacities_out, float* g_scales,
+                                float* g_opacities, void* stream);
+
 /* For tests of failure detection: the onesweep radix sort's look-back waits
  * on its predecessor partitions, each wait bounded by spin_limit polls (0
  * restores the default, about a second); after that it writes

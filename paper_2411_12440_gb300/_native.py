@@ -35,6 +35,13 @@ class LsMlp(ctypes.Structure):
                 ("b2", ctypes.c_void_p), ("w3", ctypes.c_void_p), ("b3", ctypes.c_void_p)]
 
 
+class LsDensifyParams(ctypes.Structure):
+    _fields_ = [("grad2d", ctypes.c_float), ("grow_scale2d", ctypes.c_float), ("grow_scale3d", ctypes.c_float),
+                ("prune_scale2d", ctypes.c_float), ("prune_scale3d", ctypes.c_float),
+                ("prune_opacity", ctypes.c_float), ("use_scale2d", ctypes.c_int32),
+                ("use_prune_scale3d", ctypes.c_int32)]
+
+
 class LsCamera(ctypes.Structure):
     _fields_ = [("viewmat", ctypes.c_float * 16), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
                 ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
@@ -82,6 +89,13 @@ PROTOTYPES = {
                              _P]),
     "ls_adam": (_I32, [_I64, _P, _P, _P, _P, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                        _I32, _P]),
+    "ls_densify_accumulate": (_I32, [_I32, _P, _P, _PC, _I32, _P, _P, _P, _P]),
+    "ls_filter3d_workspace": (_SZ, []),
+    "ls_filter3d_variance": (_I32, [_I32, _P, _PC, _I32, ctypes.c_float, ctypes.c_float, _P, _P, _SZ, _P]),
+    "ls_filter3d_apply": (_I32, [_I32, _P, _P, _P, _P, _P, _P]),
+    "ls_filter3d_apply_bwd": (_I32, [_I32, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ls_densify_decide": (_I32, [_I32, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.POINTER(LsDensifyParams), _P, _P,
+                                 _P]),
 }
 
 _lib = None

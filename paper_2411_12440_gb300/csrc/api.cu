@@ -508,6 +508,69 @@ ls_status ls_adam(int64_t n, float* param, const float* grad, float* m1, float* 
   return LS_OK;
 }
 
+ls_status ls_densify_accumulate(int32_t n, const float* g2d, const void* proj, const ls_camera* cam, int32_t n_cams,
+                                float* grad_accum, int32_t* count, float* max_radius, void* stream) {
+  if (n < 0 || n_cams < 1 || !cam || !cam_ok(*cam)) return LS_ERR_INVALID_ARG;
+  if (n > 0 && (!g2d || !proj || !grad_accum || !count || !max_radius)) return LS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(proj) % 16) return LS_ERR_INVALID_ARG;
+  ProjCPtr pp = proj_cplanes(proj, n);
+  LS_TRY(launch_densify_accum(n, g2d, pp.foot, pp.dkey, cam->width, cam->height, n_cams, grad_accum, count,
+                              max_radius, static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+ls_status ls_densify_decide(int32_t n, const float* grad_accum, const int32_t* count, const float* max_radius,
+                            const float* scales, const float* opacities, float scene_extent,
+                            const ls_densify_params* params, uint8_t* flags, int64_t* counts_dev, void* stream) {
+  if (n < 0 || !params || !(scene_extent > 0.f) || !std::isfinite(scene_extent)) return LS_ERR_INVALID_ARG;
+  if (n > 0 && (!grad_accum || !count || !max_radius || !scales || !opacities || !flags)) return LS_ERR_INVALID_ARG;
+  LS_TRY(launch_densify_decide(n, grad_accum, count, max_radius, scales, opacities, scene_extent, *params, flags,
+                               counts_dev, static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+size_t ls_filter3d_workspace(void) { return 256; }
+
+ls_status ls_filter3d_variance(int32_t n, const float* means, const ls_camera* cams, int32_t n_cams, float near_plane,
+                               float s2, float* filter_var, void* workspace, size_t ws_bytes, void* stream) {
+  if (n < 0 || !(near_plane > 0.f) || !(s2 >= 0.f) || !std::isfinite(s2)) return LS_ERR_INVALID_ARG;
+  if (!workspace || ws_bytes < ls_filter3d_workspace() || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return LS_ERR_INVALID_ARG;
+  ls_params p{};
+  p.lambda = 1.f;
+  p.alpha_max = 0.5f;
+  p.tile_w = p.tile_h = 16;
+  p.near_plane = near_plane;
+  p.far_plane = 2.f * near_plane + 1.f;
+  CamTable T;
+  if (!make_cams(cams, n_cams, &p, T, nullptr)) return LS_ERR_INVALID_ARG;
+  if (n > 0 && (!means || !filter_var)) return LS_ERR_INVALID_ARG;
+  LS_TRY(launch_filter3d_variance(n, means, T, near_plane, s2, filter_var, static_cast<unsigned*>(workspace),
+                                  static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+ls_status ls_filter3d_apply(int32_t n, const float* scales, const float* opacities, const float* filter_var,
+                            float* scales_out, float* opacities_out, void* stream) {
+  if (n < 0) return LS_ERR_INVALID_ARG;
+  if (n > 0 && (!scales || !opacities || !filter_var || !scales_out || !opacities_out)) return LS_ERR_INVALID_ARG;
+  LS_TRY(launch_filter3d_apply(n, scales, opacities, filter_var, scales_out, opacities_out,
+                               static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
+ls_status ls_filter3d_apply_bwd(int32_t n, const float* scales, const float* opacities, const float* filter_var,
+                                const float* g_scales_out, const float* g_opacities_out, float* g_scales,
+                                float* g_opacities, void* stream) {
+  if (n < 0) return LS_ERR_INVALID_ARG;
+  if (n > 0 && (!scales || !opacities || !filter_var || !g_scales_out || !g_opacities_out || !g_scales ||
+                !g_opacities))
+    return LS_ERR_INVALID_ARG;
+  LS_TRY(launch_filter3d_apply_bwd(n, scales, opacities, filter_var, g_scales_out, g_opacities_out, g_scales,
+                                   g_opacities, static_cast<cudaStream_t>(stream)));
+  return LS_OK;
+}
+
 // ---------------------------------------------------------------- termination MLP
 namespace {
 bool mlp_ok(const ls_mlp* n) { return n && n->w1t && n->b1 && n->w2t && n->b2 && n->w3 && n->b3; }

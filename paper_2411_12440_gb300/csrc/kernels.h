@@ -250,6 +250,19 @@ cudaError_t launch_image_loss(int H, int W, const float* pred, const float* targ
                               float* loss_out, float* grad, void* ws, cudaStream_t st);
 cudaError_t launch_adam(int64_t n, float* p, const float* g, float* m, float* v, int step, float lr, float b1,
                         float b2, float eps, int mode, cudaStream_t st);
+cudaError_t launch_densify_accum(int n, const float* g2d, const float4* foot, const uint32_t* dkey, int W, int H,
+                                 int n_cams, float* accum, int32_t* count, float* max_radius, cudaStream_t st);
+cudaError_t launch_densify_decide(int n, const float* accum, const int32_t* count, const float* max_radius,
+                                  const float* scales, const float* opac, float extent, const ls_densify_params& p,
+                                  uint8_t* flags, int64_t* counts, cudaStream_t st);
+
+// ---- 3D smoothing filter of the anti-aliased variant (filter3d.cu)
+cudaError_t launch_filter3d_variance(int n, const float* means, const CamTable& cams, float near_plane, float s2,
+                                     float* var, unsigned* max_bits, cudaStream_t st);
+cudaError_t launch_filter3d_apply(int n, const float* scales, const float* opac, const float* var, float* s_out,
+                                  float* o_out, cudaStream_t st);
+cudaError_t launch_filter3d_apply_bwd(int n, const float* scales, const float* opac, const float* var,
+                                      const float* g_se, const float* g_oe, float* g_s, float* g_o, cudaStream_t st);
 
 // ---- termination MLP (mlp.cu)
 struct MlpDev {

@@ -250,6 +250,70 @@ __global__ void __launch_bounds__(256) adam_kernel(int64_t n, float* __restrict_
   }
 }
 
+// Densification statistics (reading of the appendix's threshold table as the
+// gsplat v1.3 default strategy applies it): per view, every primitive whose
+// support box meets the image adds |(dL/dmx W/2 n, dL/dmy H/2 n)| to its
+// accumulator, counts the view and keeps its largest support radius over
+// max(W, H).  Binary32, each operation rounded once.
+__global__ void __launch_bounds__(256) densify_accum_kernel(int n, const float* __restrict__ g2d,
+                                                            const float4* __restrict__ foot,
+                                                            const uint32_t* __restrict__ dkey, int W, int H,
+                                                            float sx, float sy, float inv_wh,
+                                                            float* __restrict__ accum, int32_t* __restrict__ count,
+                                                            float* __restrict__ max_radius) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || dkey[i] == DKEY_CULLED) return;
+  const float4 f = foot[i];
+  int tx0, tx1, ty0, ty1;
+  if (!tile_rect(f.x, f.y, f.z, f.w, W, H, 1, 1, tx0, tx1, ty0, ty1)) return;
+  const float gx = __fmul_rn(g2d[12 * (size_t)i], sx), gy = __fmul_rn(g2d[12 * (size_t)i + 1], sy);
+  const float nrm = __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
+  accum[i] = __fadd_rn(accum[i], nrm);
+  count[i] += 1;
+  max_radius[i] = fmaxf(max_radius[i], __fmul_rn(fmaxf(f.z, f.w), inv_wh));
+}
+
+struct DensifyTh {
+  float grad2d, grow2d, grow3d_ext, prune2d, prune3d_ext, prune_opac;
+  int use2d, use_prune3d;
+};
+
+// Flags: bit 0 duplicate, bit 1 split, bit 2 prune; counts[3] of each.
+__global__ void __launch_bounds__(256) densify_decide_kernel(int n, const float* __restrict__ accum,
+                                                             const int32_t* __restrict__ count,
+                                                             const float* __restrict__ max_radius,
+                                                             const float* __restrict__ scales,
+                                                             const float* __restrict__ opac, const DensifyTh th,
+                                                             uint8_t* __restrict__ flags,
+                                                             unsigned long long* __restrict__ counts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned fl = 0u;
+  if (i < n) {
+    const float g = __fdiv_rn(accum[i], (float)max(count[i], 1));
+    const float smax = fmaxf(fmaxf(scales[3 * (size_t)i], scales[3 * (size_t)i + 1]), scales[3 * (size_t)i + 2]);
+    const bool grow = g > th.grad2d;
+    const bool small = smax <= th.grow3d_ext;
+    bool split = grow && !small;
+    bool prune = opac[i] < th.prune_opac;
+    if (th.use_prune3d) prune = prune || smax > th.prune3d_ext;
+    if (th.use2d) {
+      split = split || max_radius[i] > th.grow2d;
+      prune = prune || max_radius[i] > th.prune2d;
+    }
+    fl = (grow && small ? 1u : 0u) | (split ? 2u : 0u) | (prune ? 4u : 0u);
+    flags[i] = (uint8_t)fl;
+  }
+  if (counts) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const unsigned c = __popc(__ballot_sync(FULL, (fl >> b) & 1u));
+      if (lane == 0 && c) atomicAdd(&counts[b], (unsigned long long)c);
+    }
+  }
+}
+
 bool g_gauss_set[64] = {false};
 
 cudaError_t ensure_gauss() {
@@ -293,6 +357,38 @@ cudaError_t launch_image_loss(int H, int W, const float* pred, const float* targ
   if (grad)
     ssim_bwd_kernel<<<grid, SS_THREADS, 0, st>>>(H, W, pred, target, mapP, mapQ, mapR, w1, w2, w3,
                                                  (float)(1.0 / (double)px), grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_densify_accum(int n, const float* g2d, const float4* foot, const uint32_t* dkey, int W, int H,
+                                 int n_cams, float* accum, int32_t* count, float* max_radius, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const float sx = ((float)W * 0.5f) * (float)n_cams, sy = ((float)H * 0.5f) * (float)n_cams;
+  const float inv_wh = 1.f / (float)(W > H ? W : H);
+  densify_accum_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, g2d, foot, dkey, W, H, sx, sy, inv_wh, accum, count,
+                                                        max_radius);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_densify_decide(int n, const float* accum, const int32_t* count, const float* max_radius,
+                                  const float* scales, const float* opac, float extent, const ls_densify_params& p,
+                                  uint8_t* flags, int64_t* counts, cudaStream_t st) {
+  if (counts) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, 3 * sizeof(int64_t), st);
+    if (e != cudaSuccess) return e;
+  }
+  if (n <= 0) return cudaSuccess;
+  DensifyTh th;
+  th.grad2d = p.grad2d;
+  th.grow2d = p.grow_scale2d;
+  th.grow3d_ext = p.grow_scale3d * extent;
+  th.prune2d = p.prune_scale2d;
+  th.prune3d_ext = p.prune_scale3d * extent;
+  th.prune_opac = p.prune_opacity;
+  th.use2d = p.use_scale2d;
+  th.use_prune3d = p.use_prune_scale3d;
+  densify_decide_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, accum, count, max_radius, scales, opac, th, flags,
+                                                         reinterpret_cast<unsigned long long*>(counts));
   return cudaGetLastError();
 }
 

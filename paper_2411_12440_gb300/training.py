@@ -75,3 +75,48 @@ class Adam:
                 continue
             adam_(getattr(self.sp, k), grads[k], self.m1[k], self.m2[k], self.step_count, lr, self.betas[0],
                   self.betas[1], self.eps, mode)
+
+
+# The densification thresholds of the appendix table (3DLS row) and the 3DGS
+# row beside it.
+DENSIFY_3DLS = dict(grad2d=0.0002, grow_scale2d=0.05, grow_scale3d=0.006, prune_scale2d=0.15, prune_scale3d=0.4,
+                    prune_opacity=0.025)
+DENSIFY_3DGS = dict(grad2d=0.0002, grow_scale2d=0.05, grow_scale3d=0.01, prune_scale2d=0.15, prune_scale3d=0.1,
+                    prune_opacity=0.005)
+
+
+class DensifyStats:
+    """Per-primitive densification statistics (ls_densify_accumulate) and
+    the refinement decision (ls_densify_decide): flags bit 0 duplicate,
+    bit 1 split, bit 2 prune."""
+
+    def __init__(self, n, device="cuda"):
+        self.n = int(n)
+        self.device = torch.device(device)
+        self.grad_accum = torch.zeros(self.n, dtype=torch.float32, device=self.device)
+        self.count = torch.zeros(self.n, dtype=torch.int32, device=self.device)
+        self.max_radius = torch.zeros(self.n, dtype=torch.float32, device=self.device)
+        self.flags = torch.zeros(self.n, dtype=torch.uint8, device=self.device)
+        self.counts = torch.zeros(3, dtype=torch.int64, device=self.device)
+
+    def reset(self):
+        self.grad_accum.zero_()
+        self.count.zero_()
+        self.max_radius.zero_()
+
+    def accumulate(self, g2d, proj, cam, n_cams=1):
+        from .raster import cam_struct
+        N.check(N.lib().ls_densify_accumulate(self.n, _p(g2d), _p(proj), ctypes.byref(cam_struct(cam)), int(n_cams),
+                                              _p(self.grad_accum), _p(self.count), _p(self.max_radius), _stream()),
+                "ls_densify_accumulate")
+
+    def decide(self, splats: Splats, extent, thresholds=DENSIFY_3DLS, use_scale2d=False, use_prune_scale3d=False):
+        p = N.LsDensifyParams()
+        for k, v in thresholds.items():
+            setattr(p, k, float(v))
+        p.use_scale2d = int(use_scale2d)
+        p.use_prune_scale3d = int(use_prune_scale3d)
+        N.check(N.lib().ls_densify_decide(self.n, _p(self.grad_accum), _p(self.count), _p(self.max_radius),
+                                          _p(splats.scales), _p(splats.opac), float(extent), ctypes.byref(p),
+                                          _p(self.flags), _p(self.counts), _stream()), "ls_densify_decide")
+        return self.flags, self.counts

@@ -59,3 +59,59 @@ def test_adam_matches_oracle(mode):
     err = np.abs(pt.cpu().numpy() - pr).max()
     log_parity("adam", mode=mode, max_abs=float(err))
     assert err < 2e-6
+
+
+def _rand_views(R, W, H, seed):
+    from paper_2411_12440_gb300 import scenes
+    from tests.gpu_helpers import pack_records
+    rec = scenes.random_records(R, W, H, seed=seed, visible_frac=0.8)
+    rec["mean2d"][: R // 10] -= 2 * max(W, H)  # some boxes entirely off the image
+    proj, dkey = pack_records(rec)
+    foot = np.concatenate([rec["mean2d"], rec["ext"]], 1).astype(np.float32)
+    return proj, foot, dkey
+
+
+def test_densify_statistics_match_oracle_bitwise():
+    """Two views accumulated on the GPU and by the binary32 reference: the
+    same bits (every operation is rounded once on both sides)."""
+    from paper_2411_12440_gb300 import scenes
+    R, W, H = 50_000, 640, 360
+    st = training.DensifyStats(R)
+    a, c, m = np.zeros(R, np.float32), np.zeros(R, np.int32), np.zeros(R, np.float32)
+    r = np.random.default_rng(9)
+    for v in range(2):
+        proj, foot, dkey = _rand_views(R, W, H, seed=20 + v)
+        g2d = (r.standard_normal((R, 12)) * 1e-5).astype(np.float32)
+        st.accumulate(torch.from_numpy(g2d).cuda(), proj, scenes.identity_camera(W, H), n_cams=1)
+        a, c, m = train.densify_accumulate(g2d, foot, dkey, W, H, 1, a, c, m)
+    torch.cuda.synchronize()
+    assert np.array_equal(st.grad_accum.cpu().numpy().view(np.uint32), a.view(np.uint32))
+    assert np.array_equal(st.count.cpu().numpy(), c)
+    assert np.array_equal(st.max_radius.cpu().numpy().view(np.uint32), m.view(np.uint32))
+    assert 0 < (c > 0).sum() < R
+
+
+@pytest.mark.parametrize("rules", [(False, False), (True, True)])
+def test_densify_decision_matches_oracle_bitwise(rules):
+    from paper_2411_12440_gb300 import raster
+    r = np.random.default_rng(11)
+    n = 100_000
+    accum = (r.random(n) * 6e-4).astype(np.float32)
+    count = r.integers(0, 4, n).astype(np.int32)
+    rad = (r.random(n) * 0.3).astype(np.float32)
+    scales = (r.random((n, 3)) ** 3 * 0.1).astype(np.float32)
+    opac = r.random(n).astype(np.float32)
+    extent = 4.0
+    want = train.densify_decide(accum, count, rad, scales, opac, extent, train.DENSIFY_3DLS, *rules)
+    st = training.DensifyStats(n)
+    st.grad_accum.copy_(torch.from_numpy(accum))
+    st.count.copy_(torch.from_numpy(count))
+    st.max_radius.copy_(torch.from_numpy(rad))
+    sp = raster.Splats(torch.zeros((n, 3), device="cuda"), torch.from_numpy(scales).cuda(),
+                       torch.zeros((n, 4), device="cuda"), torch.from_numpy(opac).cuda(), torch.zeros((3, n), device="cuda"), 0)
+    flags, counts = st.decide(sp, extent, training.DENSIFY_3DLS, *rules)
+    torch.cuda.synchronize()
+    got = flags.cpu().numpy()
+    assert np.array_equal(got, want)
+    assert counts.cpu().tolist() == [int(((want >> b) & 1).sum()) for b in range(3)]
+    assert all(0 < int(((want >> b) & 1).sum()) < n for b in range(3))

@@ -101,3 +101,90 @@ def test_adam_first_step_moves_by_lr():
     o1, _, _ = train.adam_step(o, g, z, z, 1, 0.01, mode=2)
     lo = np.log(o / (1 - o))
     assert np.allclose(np.log(o1 / (1 - o1)), lo - 0.01 * np.sign(g), rtol=1e-9, atol=1e-12)
+
+
+def test_densify_accumulate_closed_form():
+    """Two primitives in a 200 x 100 view, one culled and one whose box lies
+    outside the image: only the first counts; its NDC gradient norm is
+    |(gx W/2, gy H/2)| = |(3e-6 * 100, -4e-6 * 50)|."""
+    g2d = np.array([[3e-6, -4e-6], [1.0, 1.0], [1.0, 1.0]], np.float32)
+    foot = np.array([[50, 50, 10, 20], [50, 50, 10, 10], [-30, 50, 5, 5]], np.float32)
+    dkey = np.array([0x40000000, 0xFFFFFFFF, 0x40000000], np.uint32)
+    a, c, r = train.densify_accumulate(g2d, foot, dkey, 200, 100, 1, np.zeros(3), np.zeros(3), np.zeros(3))
+    assert a[0] == pytest.approx(math.hypot(3e-6 * 100, 4e-6 * 50), rel=1e-6) and a[1] == 0 and a[2] == 0
+    assert list(c) == [1, 0, 0] and r[0] == pytest.approx(20 / 200) and r[1] == 0
+    a2, c2, r2 = train.densify_accumulate(g2d, foot, dkey, 200, 100, 2, a, c, r)
+    assert a2[0] == pytest.approx(3 * a[0], rel=1e-6) and c2[0] == 2
+
+
+def test_densify_decide_rules():
+    """The thresholds of the appendix table (3DLS row) on hand-made cases."""
+    th = train.DENSIFY_3DLS
+    ext = 10.0
+    #            grad high, small   grad high, large   grad low         faint          huge 3D
+    accum = np.array([3e-4, 3e-4, 1e-4, 0.0, 0.0], np.float32)
+    count = np.array([1, 1, 1, 0, 1], np.int32)
+    scales = np.array([[0.05, 0.01, 0.01], [0.07, 0.01, 0.01], [0.01] * 3, [0.01] * 3, [5.0, 1, 1]], np.float32)
+    opac = np.array([0.5, 0.5, 0.5, 0.02, 0.5], np.float32)
+    rad = np.array([0.0, 0.0, 0.2, 0.0, 0.0], np.float32)
+    f = train.densify_decide(accum, count, rad, scales, opac, ext, th)
+    assert list(f) == [1, 2, 0, 4, 0]  # 0.05 <= 0.006 * 10 < 0.07
+    f = train.densify_decide(accum, count, rad, scales, opac, ext, th, use_scale2d=True, use_prune_scale3d=True)
+    assert list(f) == [1, 2, 2 | 4, 4, 4]  # radius 0.2 > 0.05 (split) and > 0.15 (prune); 5 > 0.4 * 10
+    # the 3DGS row of the same table grows at 0.01 * extent instead
+    f = train.densify_decide(accum, count, rad, scales, opac, ext, train.DENSIFY_3DGS)
+    assert list(f) == [1, 1, 0, 0, 0]  # 0.07 <= 0.1; opacity 0.02 >= 0.005
+
+
+def _cam(fx, W=200, H=100, vm=None):
+    from paper_2411_12440_gb300 import scenes
+    return scenes.camera(np.eye(4) if vm is None else vm, fx, fx, W / 2, H / 2, W, H)
+
+
+def test_filter3d_variance_closed_forms():
+    """On the axis at depth z: v = 0.2 (z / fx)^2; two cameras: the nearer /
+    longer-focal one decides; outside every frustum: the largest v."""
+    means = np.array([[0.0, 0.0, 4.0], [0.0, 0.0, 2.0], [100.0, 0.0, 1.0]])
+    v = train.filter3d_variance(means, [_cam(100.0)])
+    assert v[0] == pytest.approx(0.2 * (4 / 100) ** 2) and v[1] == pytest.approx(0.2 * (2 / 100) ** 2)
+    assert v[2] == pytest.approx(v[0])  # x = 100 * 100 + 100 is far outside: takes the largest
+    v2 = train.filter3d_variance(means, [_cam(100.0), _cam(300.0)])
+    assert v2[0] == pytest.approx(0.2 * (4 / 300) ** 2)
+    # the 1.15 margin: a centre at x = 1.1 W is seen, at 1.2 W it is not
+    m = np.array([[(1.1 * 200 - 100) * 4 / 100, 0, 4.0], [(1.2 * 200 - 100) * 4 / 100, 0, 4.0], [0, 0, 8.0]])
+    v3 = train.filter3d_variance(m, [_cam(100.0)])
+    assert v3[0] == pytest.approx(0.2 * 0.04 ** 2) and v3[1] == pytest.approx(v3[2]) == pytest.approx(0.2 * 0.08 ** 2)
+
+
+def test_filter3d_keeps_opacity_times_volume():
+    """o sqrt(det Sigma) = o prod(scales) is what the filter keeps."""
+    r = np.random.default_rng(4)
+    s = r.random((50, 3)) * 0.1 + 1e-3
+    o = r.random(50)
+    v = r.random(50) * 1e-3
+    se, oe = train.filter3d_apply(s, o, v)
+    assert np.allclose(oe * se.prod(1), o * s.prod(1), rtol=1e-13)
+    assert np.allclose(se ** 2 - s ** 2, v[:, None], rtol=1e-12, atol=1e-18)
+    se0, oe0 = train.filter3d_apply(s, o, np.zeros(50))
+    assert np.array_equal(se0, s) and np.allclose(oe0, o, rtol=1e-15)
+
+
+def test_filter3d_gradient_finite_differences():
+    r = np.random.default_rng(5)
+    s = r.random((6, 3)) * 0.1 + 0.01
+    o = r.random(6)
+    v = r.random(6) * 1e-3
+    ws, wo = r.standard_normal((6, 3)), r.standard_normal(6)
+    f = lambda s_, o_: (train.filter3d_apply(s_, o_, v)[0] * ws).sum() + (train.filter3d_apply(s_, o_, v)[1] * wo).sum()
+    g_s, g_o = train.filter3d_apply_bwd(s, o, v, ws, wo)
+    h = 1e-7
+    for i in range(6):
+        for k in range(3):
+            sp, sm = s.copy(), s.copy()
+            sp[i, k] += h
+            sm[i, k] -= h
+            assert g_s[i, k] == pytest.approx((f(sp, o) - f(sm, o)) / (2 * h), rel=1e-6, abs=1e-9)
+        op, om = o.copy(), o.copy()
+        op[i] += h
+        om[i] -= h
+        assert g_o[i] == pytest.approx((f(s, op) - f(s, om)) / (2 * h), rel=1e-6, abs=1e-9)
