@@ -476,6 +476,8 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
           s_q[r] += gq;
         }
       }
+      const unsigned bal = __ballot_sync(FULL, any);
+      if (bal == 0u) continue;
       // A d = L^T (L d) = (l00 e1, l01 e1 + l11 e2): the conic-space mean
       // gradient and the conic-entry gradients (b counted once)
       float v[9];
@@ -495,8 +497,6 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
       v[6] = v6;
       v[7] = v7;
       v[8] = v8;
-      const unsigned bal = __ballot_sync(FULL, any);
-      if (bal == 0u) continue;
       if (__popc(bal) == 1) {
         if (any) {
 #pragma unroll
