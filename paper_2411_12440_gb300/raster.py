@@ -210,7 +210,7 @@ class Rasterizer:
         total_tiles = sum(tiles_of(c, P) for c in cams)
         keys = self._buf("keys", 4 * max(cap, 1), torch.int32)
         vals = self._buf("vals", 4 * max(cap, 1), torch.int32)
-        n_keys = torch.zeros(1, dtype=torch.int64, device=self.device)
+        n_keys = torch.empty(1, dtype=torch.int64, device=self.device)  # written by the call
         ranges = torch.empty(2 * total_tiles, dtype=torch.int32, device=self.device)
         wsb = N.lib().ls_duplicate_sort_workspace(R, cap, total_tiles)
         ws = self._buf("dup_ws", wsb + 256)
