@@ -135,3 +135,38 @@ def test_debug_sort_wait_setter_checks_arguments(L):
     assert L.ls_debug_set_sort_wait(0, -2) == 1
     assert L.ls_debug_set_sort_wait(1000, 0) == 0
     assert L.ls_debug_set_sort_wait(0, -1) == 0  # defaults again
+
+
+def test_training_entry_points_reject_bad_arguments_before_launch(L):
+    """The loss, Adam, densification and 3D-filter entry points check their
+    arguments on the host (no pointer is dereferenced here)."""
+    from paper_2411_12440_gb300 import _native as N
+    from paper_2411_12440_gb300 import raster, scenes
+    fake = ctypes.c_void_p(256)
+    assert L.ls_image_loss_workspace(0, 10) == 0 and L.ls_image_loss_workspace(10, 20000) == 0
+    assert L.ls_image_loss_workspace(10, 20) > 0
+    ws = L.ls_image_loss_workspace(10, 20)
+    assert L.ls_image_loss(0, 20, fake, fake, 0.6, 0.2, 0.2, fake, fake, fake, ws, None) == 1
+    assert L.ls_image_loss(10, 20, None, fake, 0.6, 0.2, 0.2, fake, fake, fake, ws, None) == 1
+    assert L.ls_image_loss(10, 20, fake, fake, float("nan"), 0.2, 0.2, fake, fake, fake, ws, None) == 1
+    assert L.ls_image_loss(10, 20, fake, fake, 0.6, 0.2, 0.2, fake, fake, fake, ws - 1, None) == 1
+    assert L.ls_image_loss(10, 20, fake, fake, 0.6, 0.2, 0.2, fake, fake, ctypes.c_void_p(300), ws, None) == 1
+    assert L.ls_adam(10, fake, fake, fake, fake, 0, 1e-3, 0.9, 0.999, 1e-15, 0, None) == 1  # step 0
+    assert L.ls_adam(10, fake, fake, fake, fake, 1, 1e-3, 0.9, 0.999, 1e-15, 3, None) == 1  # mode 3
+    assert L.ls_adam(10, fake, fake, fake, fake, 1, 1e-3, 1.0, 0.999, 1e-15, 0, None) == 1  # beta1 1
+    assert L.ls_adam(0, None, None, None, None, 1, 1e-3, 0.9, 0.999, 1e-15, 0, None) == 0  # nothing to do
+    cam = raster.cam_struct(scenes.identity_camera(64, 64))
+    assert L.ls_densify_accumulate(10, fake, fake, ctypes.byref(cam), 0, fake, fake, fake, None) == 1
+    assert L.ls_densify_accumulate(10, fake, ctypes.c_void_p(260), ctypes.byref(cam), 1, fake, fake, fake,
+                                   None) == 1  # misaligned records
+    p = N.LsDensifyParams()
+    assert L.ls_densify_decide(10, fake, fake, fake, fake, fake, 0.0, ctypes.byref(p), fake, None, None) == 1
+    assert L.ls_densify_decide(10, fake, fake, fake, fake, fake, 1.0, None, fake, None, None) == 1
+    cams = raster.cam_array([scenes.identity_camera(64, 64)])
+    wsf = L.ls_filter3d_workspace()
+    assert L.ls_filter3d_variance(10, fake, cams, 1, 0.0, 0.2, fake, fake, wsf, None) == 1  # near 0
+    assert L.ls_filter3d_variance(10, fake, cams, 0, 0.2, 0.2, fake, fake, wsf, None) == 1  # no camera
+    assert L.ls_filter3d_variance(10, fake, cams, 1, 0.2, 0.2, fake, ctypes.c_void_p(300), wsf, None) == 1
+    assert L.ls_filter3d_apply(-1, fake, fake, fake, fake, fake, None) == 1
+    assert L.ls_filter3d_apply_bwd(10, fake, None, fake, fake, fake, fake, fake, None) == 1
+    assert L.ls_filter3d_apply(0, None, None, None, None, None, None) == 0
