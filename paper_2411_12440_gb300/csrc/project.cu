@@ -184,10 +184,11 @@ __device__ __forceinline__ bool proj_geometry(const float* mu, const float* sc, 
   return true;
 }
 
-// Four CTAs per SM (at most 64 registers): more loads in flight, 5 % faster
-// than the 80-register build at three.
+// Five CTAs per SM (at most 48 registers, no spills): more loads in flight;
+// 5 % faster than three CTAs at 80 registers, 2 % faster than four at 64
+// (six, at 40 registers, spill and are not faster).
 template <int DEG>
-__global__ void __launch_bounds__(256, 4) project_fwd_kernel(int n, const float* __restrict__ means,
+__global__ void __launch_bounds__(256, 5) project_fwd_kernel(int n, const float* __restrict__ means,
                                                           const float* __restrict__ scales,
                                                           const float4* __restrict__ quats,
                                                           const float* __restrict__ opac,
