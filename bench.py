@@ -118,6 +118,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def frame_config(prims, cam, tile, ws, prims_override):
+    """The `config` of the measured frame, the same for both arms."""
+    wl = WORKLOAD if prims_override is None else "%s (prims=%d)" % (WORKLOAD, prims)
+    return {"workload": wl, "prims": prims, "width": cam["width"], "height": cam["height"], "sh_degree": 3,
+            "tile": "%dx%d" % (tile, tile), "l2": "inputs larger than L2 (708 MB of parameters)",
+            "parallelism": "replicas" if ws > 1 else "single"}
+
+
 class Peaks:
     """Roofline denominators: the measured HBM copy rate (MEASURED_PEAKS.json)
     and the FP32 lane rate SMs x 128 lanes x the maximum SM clock, the SM
@@ -279,9 +287,13 @@ def run_reference(args):
     ncores = os.cpu_count() or 1
     scene, cams, extra = scenes.make_workload(WORKLOAD)
     P = dict(sh_degree=3, antialias=int(extra["antialias"]))
-    # a sample is several seconds of host work: at most one warm-up and three
-    # timed steps keep the arm within a minute or two
-    steps, warmup = max(1, min(args.steps, 3)), min(args.warmup, 1)
+    # each step is one bounded sample (~9 s of host work on 16 cores); the
+    # steps and warm-up steps asked for are run as given unless that would
+    # take more than ~6 minutes
+    steps, warmup = max(1, args.steps), max(0, args.warmup)
+    if steps + warmup > 40:
+        warmup = min(warmup, 2)
+        steps = max(1, min(steps, 40 - warmup))
     ests, spent = [], []
     sample = ""
     for i in range(warmup + steps):
@@ -296,8 +308,7 @@ def run_reference(args):
             "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * statistics.mean(spent),
             "frame_seconds_estimate": sec, "frame_seconds_estimates": [round(e, 3) for e in ests],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "prims": scene.n, "width": cams[0]["width"],
-                       "height": cams[0]["height"], "sh_degree": 3},
+            "config": frame_config(scene.n, cams[0], 16, ws, None),
             "cpu_baseline": {"value": value, "unit": "iters/s", "cores": ncores, "kind": "oracle",
                              "sample": sample, "estimate": "value extrapolates the sample to the whole frame; "
                                                            "ms_per_step is the time one sample took"},
@@ -886,10 +897,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.prims is None else "%s (prims=%d)" % (WORKLOAD, R), "prims": R,
-                       "width": W, "height": H, "sh_degree": 3,
-                       "tile": "%dx%d" % (P.tile_w, P.tile_h), "l2": "inputs larger than L2 (708 MB of parameters)",
-                       "parallelism": "replicas" if ws > 1 else "single"},
+            "config": frame_config(R, cam, P.tile_w, ws, args.prims),
             "fwd_fps": job_rate(ws, fwd_ms), "fwd_ms": fwd_ms,
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "kernels_ms": {k: round(v, 4) for k, v in kernel_ms.items()},
