@@ -16,16 +16,6 @@ from tests.gpu_helpers import GRAD_TOL, log_parity, rel_l2
 pytestmark = pytest.mark.gpu
 
 
-def test_patterns_recipe():
-    p = fitting.pattern("stripes", 4, 64)
-    assert p.shape == (64, 64, 3) and set(np.unique(p)) == {np.float32(0.1), np.float32(0.9)}
-    assert (p[:, :8] == np.float32(0.9)).all() and (p[:, 8:16] == np.float32(0.1)).all()  # 4 periods of 16 px
-    c = fitting.pattern("checkerboard", 2, 32)
-    assert c[0, 0, 0] != c[0, 8, 0] and c[0, 0, 0] != c[8, 0, 0] and c[0, 0, 0] == c[8, 8, 0]
-    r = fitting.pattern("circles", 2, 64)
-    assert r[32, 32, 0] == np.float32(0.9) and r[32, 32 + 9, 0] == np.float32(0.1)
-
-
 @pytest.mark.parametrize("kind", fitting.PATTERNS)
 def test_fit_lowers_the_loss(kind):
     out = fitting.fit(kind, 4, "linear", size=128, n_side=24, steps=150)
