@@ -728,7 +728,14 @@ def main():
     rz.check_status("warmup")
 
     # ---------------------------------------------------------------- timed fwd+bwd
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stage_names) + 1)] for _ in range(args.steps)]
+    # The headline: the frame's boundary calls recorded once in a CUDA graph
+    # (raster.FrameGraph) and replayed, as a training loop runs them; each
+    # replay redoes the whole frame on the resident parameters.
+    fg = raster.FrameGraph(rz, sp, cam, gimg, gT)
+    for _ in range(args.warmup):
+        fg.replay()
+    torch.cuda.synchronize()
+    rz.check_status("graph warmup")
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     barrier(ws)
@@ -736,12 +743,28 @@ def main():
     with ClockSampler(local) as clocks:
         t_start.record()
         for i in range(args.steps):
-            step(evs[i])
+            fg.replay()
         t_end.record()
         torch.cuda.synchronize()
     barrier(ws)
     total_ms = max_over_ranks(t_start.elapsed_time(t_end), ws)
     rz.check_status("timed steps")
+
+    # The same steps launched call by call from the host, with events between
+    # the boundary calls for the per-stage times.
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stage_names) + 1)] for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    t_e0 = torch.cuda.Event(enable_timing=True)
+    t_e1 = torch.cuda.Event(enable_timing=True)
+    t_e0.record()
+    for i in range(args.steps):
+        step(evs[i])
+    t_e1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    eager_ms = max_over_ranks(t_e0.elapsed_time(t_e1), ws) / args.steps
+    rz.check_status("call-by-call steps")
     stage_ms = {nm: statistics.mean(e[j].elapsed_time(e[j + 1]) for e in evs) for j, nm in enumerate(stage_names)}
 
     # ---------------------------------------------------------------- kernel by kernel
@@ -758,18 +781,22 @@ def main():
                  for j, nm in enumerate(kernel_names)}
 
     # ---------------------------------------------------------------- timed fwd only
+    fgf = raster.FrameGraph(rz, sp, cam)
+    for _ in range(args.warmup):
+        fgf.replay()
     barrier(ws)
     torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record()
     for i in range(args.steps):
-        step(bwd=False)
+        fgf.replay()
     f1.record()
     torch.cuda.synchronize()
     barrier(ws)
     fwd_ms = max_over_ranks(f0.elapsed_time(f1), ws) / args.steps
     rz.check_status("timed forward")
+    del fgf
 
     # ---------------------------------------------------------------- e2e through host buffers
     # Every step copies its inputs (all primitive parameters and the loss
@@ -785,10 +812,13 @@ def main():
             dev_in = [torch.empty_like(t, device=dev) for t in host_in]
             slots.append(dict(
                 dev_in=dev_in, splats=raster.Splats(*dev_in[:5], sp.sh_degree),
-                grads={k: torch.empty_like(getattr(sp, k)) for k in names},
-                image=torch.empty((H, W, 3), dtype=torch.float32, device=dev),
                 host_out=[torch.empty((H, W, 3), dtype=torch.float32).pin_memory()] +
                          [torch.empty(getattr(sp, k).shape, dtype=torch.float32).pin_memory() for k in names]))
+        for sl in slots:  # each slot's frame recorded once, on its own input buffers
+            for d_, h_ in zip(sl["dev_in"], host_in):
+                d_.copy_(h_)
+            sl["fg"] = raster.FrameGraph(rz, sl["splats"], cam, sl["dev_in"][5], sl["dev_in"][6])
+            sl["grads"], sl["image"] = sl["fg"].grads, sl["fg"].image
         h2d = sum(t.numel() * t.element_size() for t in host_in)
         d2h = sum(t.numel() * t.element_size() for t in slots[0]["host_out"])
         NS = 1  # copy streams per direction (more did not raise the host-link rate)
@@ -828,9 +858,7 @@ def main():
                 if down_done[i % 2] is not None:
                     for ev in down_done[i % 2]:  # step i-2's results are on the host
                         s_comp.wait_event(ev)
-                image, T, g = step(splats=sl["splats"], grad_image=sl["dev_in"][5], grad_t=sl["dev_in"][6],
-                                   outg=sl["grads"])
-                sl["image"].copy_(image, non_blocking=True)
+                sl["fg"].replay()  # writes sl["image"] and sl["grads"]
                 cd = torch.cuda.Event()
                 cd.record(s_comp)
                 comp_done[i % 2] = cd
@@ -857,7 +885,8 @@ def main():
         e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws) / n_e2e
         rz.check_status("e2e")
         e2e = {"value": job_rate(ws, e2e_ms), "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "overlap": "uploads, compute and read-backs on three streams, double-buffered",
+               "overlap": "uploads, compute (one frame graph per buffer) and read-backs on three streams, "
+                          "double-buffered",
                "moves": "every primitive parameter in, the image and every parameter gradient out"}
 
         # The same steps with the primitives resident on the device, as in a
@@ -867,9 +896,12 @@ def main():
         # device for the optimiser.
         r_in = [gimg.cpu().pin_memory(), gT.cpu().pin_memory()]
         r_slots = [dict(dev_in=[torch.empty_like(t, device=dev) for t in r_in],
-                        image=torch.empty((H, W, 3), dtype=torch.float32, device=dev),
-                        host_out=[torch.empty((H, W, 3), dtype=torch.float32).pin_memory()],
-                        grads={k: torch.empty_like(getattr(sp, k)) for k in names}) for _ in range(2)]
+                        host_out=[torch.empty((H, W, 3), dtype=torch.float32).pin_memory()]) for _ in range(2)]
+        for sl in r_slots:
+            for d_, h_ in zip(sl["dev_in"], r_in):
+                d_.copy_(h_)
+            sl["fg"] = raster.FrameGraph(rz, sp, cam, sl["dev_in"][0], sl["dev_in"][1])
+            sl["grads"], sl["image"] = sl["fg"].grads, sl["fg"].image
         r_h2d = sum(t.numel() * t.element_size() for t in r_in)
         r_d2h = sum(t.numel() * t.element_size() for t in r_slots[0]["host_out"])
         comp_done = [None, None]
@@ -884,8 +916,7 @@ def main():
                 if down_done[i % 2] is not None:
                     for ev in down_done[i % 2]:
                         s_comp.wait_event(ev)
-                image, T, g = step(grad_image=sl["dev_in"][0], grad_t=sl["dev_in"][1], outg=sl["grads"])
-                sl["image"].copy_(image, non_blocking=True)
+                sl["fg"].replay()
                 cd = torch.cuda.Event()
                 cd.record(s_comp)
                 comp_done[i % 2] = cd
@@ -952,6 +983,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": frame_config(R, cam, P.tile_w, ws, args.prims),
+            "launch": "the frame's boundary calls recorded once in a CUDA graph (raster.FrameGraph) and replayed",
+            "call_by_call": {"value": job_rate(ws, eager_ms), "ms_per_step": eager_ms,
+                             "launch": "the same boundary calls launched one by one from the host"},
             "fwd_fps": job_rate(ws, fwd_ms), "fwd_ms": fwd_ms,
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "kernels_ms": {k: round(v, 4) for k, v in kernel_ms.items()},

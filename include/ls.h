@@ -443,6 +443,17 @@ ls_status ls_filter3d_apply_bwd(int32_t n, const float* scales, const float* opa
  * hold_partition < -1. */
 ls_status ls_debug_set_sort_wait(int32_t spin_limit, int32_t hold_partition);
 
+/* Launch mode of the kernels of a frame (ls_project, ls_duplicate_sort,
+ * ls_render_fwd, ls_render_bwd and their parts): on = 1 (the default) lets
+ * each kernel be scheduled while the one before it in the stream finishes
+ * (programmatic dependent launch; each kernel still waits for its
+ * predecessor's results before it reads or writes anything), except while
+ * the stream is being captured into a CUDA graph, where launches stay plain;
+ * on = 0 launches them plainly always.  Results are the same either way.
+ * Process-wide, not thread-safe; LS_ERR_INVALID_ARG for other values of
+ * on. */
+ls_status ls_set_dependent_launch(int32_t on);
+
 /* Text of a status code (static storage). */
 const char* ls_status_string(int32_t status);
 

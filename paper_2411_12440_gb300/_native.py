@@ -84,6 +84,7 @@ PROTOTYPES = {
     "ls_copy": (_I32, [_P, _P, _SZ, _P]),
     "ls_fp32_issue_probe": (_I32, [_I64, _I32, _P, ctypes.POINTER(ctypes.c_int64), _P]),
     "ls_debug_set_sort_wait": (_I32, [_I32, _I32]),
+    "ls_set_dependent_launch": (_I32, [_I32]),
     "ls_image_loss_workspace": (_SZ, [_I32, _I32]),
     "ls_image_loss": (_I32, [_I32, _I32, _P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P, _P, _SZ,
                              _P]),

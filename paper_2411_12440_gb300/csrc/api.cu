@@ -158,6 +158,12 @@ DupWs dup_layout(char* base, int64_t R, int64_t cap, int key_passes) {
 
 }  // namespace
 
+namespace {
+bool g_chain_launch = true;
+}
+bool ls::chain_launch_on() { return g_chain_launch; }
+void ls::set_chain_launch(bool on) { g_chain_launch = on; }
+
 bool ls::host_total_tiles(const ls_camera* cams, int n_cams, const ls_params* p, int64_t* total_tiles) {
   if (!params_ok(p)) return false;
   CamTable T;
@@ -171,6 +177,12 @@ int32_t ls_version(void) { return 1; }
 ls_status ls_debug_set_sort_wait(int32_t spin_limit, int32_t hold_partition) {
   if (spin_limit < 0 || hold_partition < -1) return LS_ERR_INVALID_ARG;
   set_sort_wait(spin_limit, hold_partition);
+  return LS_OK;
+}
+
+ls_status ls_set_dependent_launch(int32_t on) {
+  if (on != 0 && on != 1) return LS_ERR_INVALID_ARG;
+  set_chain_launch(on == 1);
   return LS_OK;
 }
 

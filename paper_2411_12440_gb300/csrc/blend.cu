@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(128) blend_fwd_kernel(const float4* __restrict
                                                         const uint32_t* __restrict__ vals, float* __restrict__ image,
                                                         float* __restrict__ t_final, int32_t* __restrict__ n_last,
                                                         unsigned long long* stats, const TruncArgs ta) {
+  chain_enter();
   extern __shared__ float4 smem[];
   // two records per thread per batch: tiles of dense scenes stop within a
   // few hundred entries, and a smaller batch gathers fewer records that no
@@ -534,6 +535,7 @@ __global__ void __launch_bounds__(128) blend_bwd_kernel(const float4* __restrict
                                                         const float* __restrict__ grad_image,
                                                         const float* __restrict__ grad_t, float* __restrict__ g2d,
                                                         int B) {
+  chain_enter();
   extern __shared__ float4 smem[];
   __shared__ int s_max;
   float* s_acc = reinterpret_cast<float*>(smem + 3 * B);
@@ -639,9 +641,10 @@ cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev&
   const int threads = P.tile_w * P.tile_h / ppt;
   const unsigned grid = (unsigned)(cam.tiles_x * cam.tiles_y);
   const size_t sm = sizeof(float4) * 3 * 2 * threads;
-#define LS_BF3(K, PP, C)                                                                                   \
-  blend_fwd_kernel<K, PP, C><<<grid, threads, sm, st>>>(rec, cam, P, ranges, vals, image, t_final, n_last, stats, \
-                                                        labels_ta)
+  cudaError_t e = cudaSuccess;
+#define LS_BF3(K, PP, C)                                                                                     \
+  e = launch_chain(blend_fwd_kernel<K, PP, C>, dim3(grid), dim3(threads), sm, st, rec, cam, P, ranges, vals, image, \
+                   t_final, n_last, stats, labels_ta)
 #define LS_BF2(K, PP)               \
   do {                              \
     if (stats) LS_BF3(K, PP, true); \
@@ -662,7 +665,7 @@ cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev&
 #undef LS_BF
 #undef LS_BF2
 #undef LS_BF3
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
@@ -676,9 +679,10 @@ cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev&
   const int B = threads;  // one record per thread per batch (2.5 % faster than two)
   const unsigned grid = (unsigned)(cam.tiles_x * cam.tiles_y);
   const size_t sm = sizeof(float4) * 3 * B + sizeof(float) * 9 * B + 2 * sizeof(uint32_t) * B;
-#define LS_BB3(K, A, PR, RT)                                                                                   \
-  blend_bwd_kernel<K, A, PR, RT><<<grid, threads, sm, st>>>(rec, cam, P, ranges, vals, t_final, n_last, grad_image, \
-                                                            grad_t, g2d, B)
+  cudaError_t e = cudaSuccess;
+#define LS_BB3(K, A, PR, RT)                                                                                  \
+  e = launch_chain(blend_bwd_kernel<K, A, PR, RT>, dim3(grid), dim3(threads), sm, st, rec, cam, P, ranges, vals, \
+                   t_final, n_last, grad_image, grad_t, g2d, B)
 #define LS_BB2(K, A)                \
   do {                              \
     if (ppr == 4) LS_BB3(K, A, 4, 1); \
@@ -701,7 +705,7 @@ cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev&
 #undef LS_BB
 #undef LS_BB2
 #undef LS_BB3
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace ls

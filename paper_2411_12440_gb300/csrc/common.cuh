@@ -110,6 +110,20 @@ __device__ __forceinline__ float kern_support(int kid, float o, float amin) {
 }
 
 // Launch helpers shared by the host-side launchers.
+// Programmatic dependent launch.  A kernel of the frame's chain is launched
+// with programmatic stream serialisation (launch_chain in kernels.h), so the
+// next kernel of the stream may be scheduled before this one has finished.
+// Every such kernel therefore starts with chain_enter(): it first waits until
+// the kernel before it in the stream has completed and its writes are
+// visible (so nothing is read or written early, and a kernel's completion
+// still implies that of every kernel before it), then allows the kernel
+// after it to be scheduled onto the SMs as they free up.  Both instructions
+// are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void chain_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace ls

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(DUP_THREADS) dup_count_kernel(int64_t R, const
                                                                 const float4* __restrict__ foot, const CamTable cams,
                                                                 int n_per_cam, const ParDev P,
                                                                 uint2* __restrict__ rect_sorted) {
+  chain_enter();
   __shared__ CamLite s_cam[LS_MAX_CAMS];
   for (int c = threadIdx.x; c < cams.n; c += blockDim.x)
     s_cam[c] = CamLite{cams.c[c].W, cams.c[c].H, cams.c[c].tiles_x, cams.c[c].tile_base};
@@ -92,6 +93,7 @@ __device__ __forceinline__ uint64_t block_sum(uint64_t x, uint64_t* s_warp) {
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) dup_reduce_kernel(int64_t n, uint32_t* counts) {
+  chain_enter();
   __shared__ uint64_t s_warp[32];
   uint32_t v[SCAN_PER];
   scan_load(counts, n, (int64_t)blockIdx.x * SCAN_CHUNK, v);
@@ -104,6 +106,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) dup_reduce_kernel(int64_t n, uin
 
 __global__ void __launch_bounds__(SCAN_THREADS) dup_scan_kernel(int64_t n, uint32_t* counts, int64_t cap,
                                                                 int64_t* n_keys, int64_t* n_valid, int32_t* status) {
+  chain_enter();
   __shared__ uint64_t s_warp[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t b0 = (int64_t)blockIdx.x * SCAN_CHUNK;
@@ -193,6 +196,7 @@ constexpr uint32_t NO_STASH = 0xFFFFFFFFu;
 // refuted tile (summed-area table `sat`).
 template <bool EMIT, int MODE>
 __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
+  chain_enter();
   __shared__ EnumRec S[ENUM_WARPS][ENUM_WARP_RECS];
   __shared__ uint4 SR[ENUM_WARPS][32];  // a step's rows with keys: {first key, first index, record, depth bits}
   __shared__ CamLite s_cam[LS_MAX_CAMS];
@@ -444,17 +448,19 @@ __global__ void __launch_bounds__(ENUM_THREADS) enum_keys_kernel(EnumArgs A) {
 cudaError_t launch_dup_count(int64_t R, const uint32_t* order, const uint32_t* dkey_sorted, const float4* foot,
                              const CamTable& cams, int n_per_cam, const ParDev& P, uint2* rect_sorted, cudaStream_t st) {
   if (R == 0) return cudaSuccess;
-  dup_count_kernel<<<ceil_div(R, DUP_THREADS), DUP_THREADS, 0, st>>>(R, order, dkey_sorted, foot, cams, n_per_cam, P,
-                                                                    rect_sorted);
-  return cudaGetLastError();
+  return launch_chain(dup_count_kernel, dim3(ceil_div(R, DUP_THREADS)), dim3(DUP_THREADS), 0, st, R, order,
+                      dkey_sorted, foot, cams, n_per_cam, P, rect_sorted);
 }
 
 cudaError_t launch_dup_scan(int64_t n, uint32_t* counts, int64_t cap, int64_t* n_keys_dev, int64_t* n_valid_dev,
                             int32_t* status, cudaStream_t st) {
   const int64_t nb = n > 0 ? ceil_div(n, SCAN_CHUNK) : 1;
-  if (nb > 1) dup_reduce_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(n, counts);
-  dup_scan_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(n, counts, cap, n_keys_dev, n_valid_dev, status);
-  return cudaGetLastError();
+  if (nb > 1) {
+    const cudaError_t e = launch_chain(dup_reduce_kernel, dim3((unsigned)nb), dim3(SCAN_THREADS), 0, st, n, counts);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_chain(dup_scan_kernel, dim3((unsigned)nb), dim3(SCAN_THREADS), 0, st, n, counts, cap, n_keys_dev,
+                      n_valid_dev, status);
 }
 
 int64_t enum_count_words(int64_t R) {
@@ -467,18 +473,16 @@ int64_t enum_warps(int64_t R) { return R > 0 ? (int64_t)ceil_div(R, ENUM_BLOCK_R
 cudaError_t launch_enum_keys(bool emit, int mode, const EnumArgs& A, cudaStream_t st) {
   if (A.R == 0) return cudaSuccess;
   const unsigned grid = ceil_div(A.R, ENUM_BLOCK_RECS);
-#define LS_EK(E, M) enum_keys_kernel<E, M><<<grid, ENUM_THREADS, 0, st>>>(A)
+#define LS_EK(E, M) launch_chain(enum_keys_kernel<E, M>, dim3(grid), dim3(ENUM_THREADS), 0, st, A)
   if (emit) {
-    if (mode == ENUM_ALL) LS_EK(true, ENUM_ALL);
-    else if (mode == ENUM_KEPT) LS_EK(true, ENUM_KEPT);
-    else LS_EK(true, ENUM_HELD);
-  } else {
-    if (mode == ENUM_ALL) LS_EK(false, ENUM_ALL);
-    else if (mode == ENUM_KEPT) LS_EK(false, ENUM_KEPT);
-    else LS_EK(false, ENUM_HELD);
+    if (mode == ENUM_ALL) return LS_EK(true, ENUM_ALL);
+    if (mode == ENUM_KEPT) return LS_EK(true, ENUM_KEPT);
+    return LS_EK(true, ENUM_HELD);
   }
+  if (mode == ENUM_ALL) return LS_EK(false, ENUM_ALL);
+  if (mode == ENUM_KEPT) return LS_EK(false, ENUM_KEPT);
+  return LS_EK(false, ENUM_HELD);
 #undef LS_EK
-  return cudaGetLastError();
 }
 
 }  // namespace ls

@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(256, 5) project_fwd_kernel(int n, const float*
                                                           const float* __restrict__ opac,
                                                           const float* __restrict__ sh, const CamTable cams,
                                                           const ParDev P, ProjPtr out, int32_t* tile_counts) {
+  chain_enter();
   constexpr int K = (DEG + 1) * (DEG + 1);
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -266,6 +267,7 @@ __global__ void __launch_bounds__(ONE ? 256 : 128, ONE ? 2 : 1) project_bwd_kern
                                                           const float4* __restrict__ g2d, float* g_means,
                                                           float* g_scales, float4* g_quats, float* g_opac,
                                                           float* g_sh) {
+  chain_enter();
   constexpr int K = (DEG + 1) * (DEG + 1);
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -426,13 +428,15 @@ cudaError_t launch_project_fwd(int n, const float* means, const float* scales, c
   if (n == 0) return cudaSuccess;
   dim3 grid(ceil_div(n, 256), cams.n);
   const float4* q4 = reinterpret_cast<const float4*>(quats);
+#define LS_PF(D) launch_chain(project_fwd_kernel<D>, grid, dim3(256), 0, st, n, means, scales, q4, opac, sh, cams, P, \
+                             out, tile_counts)
   switch (P.sh_degree) {
-    case 0: project_fwd_kernel<0><<<grid, 256, 0, st>>>(n, means, scales, q4, opac, sh, cams, P, out, tile_counts); break;
-    case 1: project_fwd_kernel<1><<<grid, 256, 0, st>>>(n, means, scales, q4, opac, sh, cams, P, out, tile_counts); break;
-    case 2: project_fwd_kernel<2><<<grid, 256, 0, st>>>(n, means, scales, q4, opac, sh, cams, P, out, tile_counts); break;
-    default: project_fwd_kernel<3><<<grid, 256, 0, st>>>(n, means, scales, q4, opac, sh, cams, P, out, tile_counts); break;
+    case 0: return LS_PF(0);
+    case 1: return LS_PF(1);
+    case 2: return LS_PF(2);
+    default: return LS_PF(3);
   }
-  return cudaGetLastError();
+#undef LS_PF
 }
 
 cudaError_t launch_project_bwd(int n, const float* means, const float* scales, const float* quats,
@@ -444,25 +448,23 @@ cudaError_t launch_project_bwd(int n, const float* means, const float* scales, c
   const float4* g4 = reinterpret_cast<const float4*>(g2d);
   float4* gq4 = reinterpret_cast<float4*>(g_quats);
 #define LS_PB(D, ONE, TB)                                                                                  \
-  project_bwd_kernel<D, ONE><<<ceil_div(n, TB), TB, 0, st>>>(n, means, scales, q4, opac, sh, cams, P, proj, g4, \
-                                                             g_means, g_scales, gq4, g_opac, g_sh)
+  launch_chain(project_bwd_kernel<D, ONE>, dim3(ceil_div(n, TB)), dim3(TB), 0, st, n, means, scales, q4, opac, sh, \
+               cams, P, proj, g4, g_means, g_scales, gq4, g_opac, g_sh)
   if (cams.n == 1) {
     switch (P.sh_degree) {
-      case 0: LS_PB(0, true, 256); break;
-      case 1: LS_PB(1, true, 256); break;
-      case 2: LS_PB(2, true, 256); break;
-      default: LS_PB(3, true, 256); break;
-    }
-  } else {
-    switch (P.sh_degree) {
-      case 0: LS_PB(0, false, 128); break;
-      case 1: LS_PB(1, false, 128); break;
-      case 2: LS_PB(2, false, 128); break;
-      default: LS_PB(3, false, 128); break;
+      case 0: return LS_PB(0, true, 256);
+      case 1: return LS_PB(1, true, 256);
+      case 2: return LS_PB(2, true, 256);
+      default: return LS_PB(3, true, 256);
     }
   }
+  switch (P.sh_degree) {
+    case 0: return LS_PB(0, false, 128);
+    case 1: return LS_PB(1, false, 128);
+    case 2: return LS_PB(2, false, 128);
+    default: return LS_PB(3, false, 128);
+  }
 #undef LS_PB
-  return cudaGetLastError();
 }
 
 }  // namespace ls

@@ -66,6 +66,7 @@ __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t* s_warp
 __global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t* __restrict__ keys, const int64_t* n_dev,
                                                          int64_t n_host, int begin_bit, int passes,
                                                          uint32_t* __restrict__ hist) {
+  chain_enter();
   __shared__ uint32_t s_h[4][RADIX];
   for (int i = threadIdx.x; i < 4 * RADIX; i += blockDim.x) (&s_h[0][0])[i] = 0;
   __syncthreads();
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t* __restr
 }
 
 __global__ void __launch_bounds__(RADIX) radix_scan_kernel(uint32_t* hist) {
+  chain_enter();
   __shared__ uint32_t s_warp[SORT_WARPS];
   uint32_t* h = hist + (size_t)blockIdx.x * RADIX;
   uint32_t v = h[threadIdx.x];
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
     uint32_t* __restrict__ vals_out, const int64_t* n_dev, int64_t n_host, int shift,
     const uint32_t* __restrict__ digit_base, uint64_t* lookback, uint32_t* part_ctr, uint2* ranges,
     int32_t* status, int spin_limit, int hold_part) {
+  chain_enter();
   constexpr uint32_t MASK = (1u << BITS) - 1u;
   constexpr int PART = SORT_THREADS * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -245,6 +248,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
 // Ranges were accumulated as (min start, ~max end) from 0xFFFFFFFF; empty
 // tiles become [0, 0).
 __global__ void __launch_bounds__(256) ranges_fixup_kernel(uint2* ranges, int total_tiles) {
+  chain_enter();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total_tiles) return;
   uint2 r = ranges[t];
@@ -282,13 +286,11 @@ cudaError_t launch_radix_hist(const uint32_t* keys, const int64_t* n_dev, int64_
   cudaError_t e = current_sm_count(&sms);
   if (e != cudaSuccess) return e;
   const int blocks = 4 * sms;
-  radix_hist_kernel<<<blocks, 256, 0, st>>>(keys, n_dev, n_host, begin_bit, passes, hist);
-  return cudaGetLastError();
+  return launch_chain(radix_hist_kernel, dim3(blocks), dim3(256), 0, st, keys, n_dev, n_host, begin_bit, passes, hist);
 }
 
 cudaError_t launch_radix_scan(uint32_t* hist, int passes, cudaStream_t st) {
-  radix_scan_kernel<<<passes, RADIX, 0, st>>>(hist);
-  return cudaGetLastError();
+  return launch_chain(radix_scan_kernel, dim3(passes), dim3(RADIX), 0, st, hist);
 }
 
 template <int BITS, int ITEMS>
@@ -315,11 +317,10 @@ static cudaError_t onesweep_launch(const uint32_t* keys_in, const uint32_t* vals
   const int64_t parts = (cap > 0 ? cap + PART - 1 : PART) / PART;
   const int64_t resident = (int64_t)sms * 4;
   const unsigned grid = (unsigned)(parts < resident ? parts : resident);
-  onesweep_kernel<BITS, ITEMS><<<grid, SORT_THREADS, sm, st>>>(
-      keys_in, vals_in, keys_out, vals_out, n_dev, n_host, shift, s.hist + (size_t)pass * RADIX,
-      s.lookback + (size_t)pass * s.parts * RADIX, s.part_ctr + pass, reinterpret_cast<uint2*>(ranges), status,
-      g_spin_limit, ranges ? g_hold_part : -1);
-  return cudaGetLastError();
+  return launch_chain(onesweep_kernel<BITS, ITEMS>, dim3(grid), dim3(SORT_THREADS), sm, st, keys_in, vals_in, keys_out,
+                      vals_out, n_dev, n_host, shift, (const uint32_t*)(s.hist + (size_t)pass * RADIX),
+                      s.lookback + (size_t)pass * s.parts * RADIX, s.part_ctr + pass,
+                      reinterpret_cast<uint2*>(ranges), status, g_spin_limit, ranges ? g_hold_part : -1);
 }
 
 cudaError_t launch_onesweep_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
@@ -345,8 +346,8 @@ void set_sort_wait(int spin_limit, int hold_part) {
 }
 
 cudaError_t launch_ranges_fixup(int32_t* ranges, int total_tiles, cudaStream_t st) {
-  ranges_fixup_kernel<<<ceil_div(total_tiles, 256), 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
-  return cudaGetLastError();
+  return launch_chain(ranges_fixup_kernel, dim3(ceil_div(total_tiles, 256)), dim3(256), 0, st,
+                      reinterpret_cast<uint2*>(ranges), total_tiles);
 }
 
 }  // namespace ls

@@ -319,6 +319,66 @@ class Rasterizer:
         return image, T, state
 
 
+
+class FrameGraph:
+    """One camera's frame recorded once in a CUDA graph and replayed.
+
+    The recorded calls are the boundary calls of a frame: ls_project,
+    ls_duplicate_sort, ls_render_fwd and, with `grad_image`, ls_render_bwd.
+    None of them reads a value back to the host (the key count stays on the
+    device), so a replay redoes the whole frame on whatever the parameter
+    tensors hold at that moment: update them in place between replays (as
+    Adam does) and never rebind them.  The outputs live in the graph's own
+    memory and are overwritten by every replay (they hold nothing before the
+    first): `image`, `T`, `n_keys` and, with a backward, the 3D gradients in
+    `grads`.  The key capacity is the
+    rasterizer's at capture time; a frame that needs more keys sets
+    LS_ERR_CAPACITY in the status word (check it, grow the capacity and
+    capture again).  Replaying saves the host launch work and the gaps
+    between the frame's ~20 kernels.
+    """
+
+    def __init__(self, rasterizer: Rasterizer, splats: Splats, cam, grad_image=None, grad_T=None):
+        if rasterizer.device.type != "cuda":
+            raise RuntimeError("FrameGraph needs a CUDA device")
+        self.rz, self.splats, self.cam = rasterizer, splats, cam
+        self.grad_image, self.grad_T = grad_image, grad_T
+        self.grads = None
+        if grad_image is not None:
+            self.grads = dict(means=torch.empty_like(splats.means), scales=torch.empty_like(splats.scales),
+                              quats=torch.empty_like(splats.quats), opac=torch.empty_like(splats.opac),
+                              sh=torch.empty_like(splats.sh))
+        if rasterizer.capacity == 0:
+            _, tc = rasterizer.project(splats, [cam], counts=True)
+            rasterizer.ensure_capacity(tc)
+        dev = rasterizer.device
+        self._frame()  # eager once: sets the kernels' shared-memory limits and sizes the scratch
+        torch.cuda.synchronize(dev)
+        rasterizer.check_status("FrameGraph eager frame")
+        self.graph = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(self.graph, stream=s):
+                self.image, self.T, self.n_keys = self._frame()
+        torch.cuda.current_stream(dev).wait_stream(s)
+
+    def _frame(self):
+        rz, sp, cam = self.rz, self.splats, self.cam
+        proj, _ = rz.project(sp, [cam], counts=False)
+        keys, vals, n_keys, ranges = rz.duplicate_sort(proj, sp.n, [cam])
+        image, T, n_last = rz.render_fwd(proj, sp.n, cam, ranges, vals)
+        if self.grads is not None:
+            state = dict(proj=proj, ranges=ranges, vals=vals, T=T, n_last=n_last)
+            rz.render_bwd(sp, cam, state, self.grad_image, self.grad_T, out=self.grads)
+        return image, T, n_keys
+
+    def replay(self):
+        """Launch the recorded frame on the current stream."""
+        self.graph.replay()
+        return self.image, self.T
+
+
 class LinearSplatFn(torch.autograd.Function):
     """Differentiable render of one camera: (means, scales, quats, opacities,
     sh[K*3, N]) -> (image [H, W, 3], T [H, W]).  The backward recomputes

@@ -137,6 +137,12 @@ def test_debug_sort_wait_setter_checks_arguments(L):
     assert L.ls_debug_set_sort_wait(0, -1) == 0  # defaults again
 
 
+def test_dependent_launch_switch_checks_arguments(L):
+    assert L.ls_set_dependent_launch(2) == 1 and L.ls_set_dependent_launch(-1) == 1
+    assert L.ls_set_dependent_launch(0) == 0
+    assert L.ls_set_dependent_launch(1) == 0  # the default again
+
+
 def test_training_entry_points_reject_bad_arguments_before_launch(L):
     """The loss, Adam, densification and 3D-filter entry points check their
     arguments on the host (no pointer is dereferenced here)."""

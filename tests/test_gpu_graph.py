@@ -1,0 +1,119 @@
+"""GPU tests of FrameGraph, a frame's boundary calls (ls_project,
+ls_duplicate_sort, ls_render_fwd, ls_render_bwd) recorded in one CUDA graph:
+a replay gives the eager frame's image bit for bit and its gradients up to
+the order of the float atomics, follows in-place parameter updates (the key
+count included), and a frame that outgrows the captured key capacity reports
+LS_ERR_CAPACITY instead of writing past it.  The frame's kernels give the
+same results launched plainly and with programmatic dependent launch."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2411_12440_gb300 import raster, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(n=12_000, seed=4, W=320, H=200):
+    scene = scenes.cluster_scene(n, seed, 3)
+    cam = scenes.ring_cameras(1, seed, w_range=(W, W + 1), h_range=(H, H + 1))[0]
+    sp = raster.Splats.from_scene(scene)
+    w, v = scenes.loss_weights(cam["height"], cam["width"], seed=seed + 1)
+    return sp, cam, torch.from_numpy(w).cuda(), torch.from_numpy(v).cuda()
+
+
+def _eager(sp, cam, gimg, gT, P):
+    rz = raster.Rasterizer(P)
+    img, T, st = rz.forward(sp, cam)
+    g = rz.render_bwd(sp, cam, st, gimg, gT)
+    torch.cuda.synchronize()
+    rz.check_status("eager")
+    return img, T, g, int(st["n_keys"].item())
+
+
+def _rel(a, b):
+    return float((a - b).norm() / max(float(b.norm()), 1e-30))
+
+
+def test_frame_graph_replay_equals_eager_frame():
+    sp, cam, gimg, gT = _setup()
+    P = raster.RenderParams(sh_degree=3, bg=(0.1, 0.2, 0.3))
+    img0, T0, g0, nk0 = _eager(sp, cam, gimg, gT, P)
+    fg = raster.FrameGraph(raster.Rasterizer(P), sp, cam, gimg, gT)
+    for _ in range(2):
+        img, T = fg.replay()
+        torch.cuda.synchronize()
+        fg.rz.check_status("replay")
+        assert torch.equal(img, img0) and torch.equal(T, T0)
+        assert int(fg.n_keys.item()) == nk0
+        for k in g0:
+            assert _rel(fg.grads[k], g0[k]) < 1e-5, k
+
+
+def test_frame_graph_follows_parameter_updates():
+    sp, cam, gimg, gT = _setup(seed=6)
+    P = raster.RenderParams(sh_degree=3)
+    rz = raster.Rasterizer(P)
+    _, tc = rz.project(sp, [cam], counts=True)
+    rz.ensure_capacity(tc)
+    rz.capacity *= 2  # room for the moved scene
+    fg = raster.FrameGraph(rz, sp, cam, gimg, gT)
+    fg.replay()
+    torch.cuda.synchronize()
+    before = fg.image.clone()
+    gen = torch.Generator(device="cpu").manual_seed(1)
+    with torch.no_grad():  # in place, as an optimiser step does
+        sp.means += (0.05 * torch.randn(sp.means.shape, generator=gen)).cuda()
+        sp.opac.mul_(0.9)
+    fg.replay()
+    torch.cuda.synchronize()
+    rz.check_status("replay after update")
+    assert not torch.equal(fg.image, before)
+    img1, T1, g1, nk1 = _eager(sp, cam, gimg, gT, P)
+    assert torch.equal(fg.image, img1) and torch.equal(fg.T, T1)
+    assert int(fg.n_keys.item()) == nk1
+    for k in g1:
+        assert _rel(fg.grads[k], g1[k]) < 1e-5, k
+
+
+def test_frame_graph_reports_capacity_overflow():
+    sp, cam, gimg, gT = _setup(seed=8)
+    P = raster.RenderParams(sh_degree=3)
+    rz = raster.Rasterizer(P)
+    _, _, st = rz.forward(sp, cam)
+    nk = int(st["n_keys"].item())
+    rz.capacity = nk  # exactly the keys of this frame
+    fg = raster.FrameGraph(rz, sp, cam, gimg, gT)
+    fg.replay()  # the outputs hold a frame only once the graph has run
+    torch.cuda.synchronize()
+    assert int(fg.n_keys.item()) == nk and int(rz.status.item()) == 0
+    with torch.no_grad():  # every primitive three times wider: more tile keys
+        sp.scales.mul_(3.0)
+    fg.replay()
+    torch.cuda.synchronize()
+    s = int(rz.status.item())
+    assert s == 3, s  # LS_ERR_CAPACITY
+    assert int(fg.n_keys.item()) > nk
+
+
+def test_dependent_launch_gives_the_plain_launch_results():
+    from paper_2411_12440_gb300 import _native as N
+    sp, cam, gimg, gT = _setup(seed=9)
+    P = raster.RenderParams(sh_degree=3)
+    outs = []
+    try:
+        for on in (0, 1):
+            assert N.lib().ls_set_dependent_launch(on) == 0
+            rz = raster.Rasterizer(P)
+            img, T, st = rz.forward(sp, cam)
+            g = rz.render_bwd(sp, cam, st, gimg, gT)
+            torch.cuda.synchronize()
+            rz.check_status("launch mode %d" % on)
+            K = int(st["n_keys"].item())
+            outs.append((img, T, st["vals"][:K].clone(), st["ranges"].clone(), g))
+    finally:
+        N.lib().ls_set_dependent_launch(1)
+    (i0, t0, v0, r0, g0), (i1, t1, v1, r1, g1) = outs
+    assert torch.equal(i0, i1) and torch.equal(t0, t1) and torch.equal(v0, v1) and torch.equal(r0, r1)
+    for k in g0:
+        assert _rel(g1[k], g0[k]) < 1e-5, k
