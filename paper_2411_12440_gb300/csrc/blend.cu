@@ -49,13 +49,23 @@ __device__ __forceinline__ float pair_q(float x, float mx, float l00, float l01d
   return __fmaf_rn(e1, e1, e2s);
 }
 
-// alpha of a pair inside the support: min(alpha_max, o f(D / lambda)).
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// alpha of a pair inside the support: min(alpha_max, o f(D / lambda)).  The
+// linear profile is one fused 1 - D / lambda: inside the support
+// D / lambda <= x_s < 1, so its clamp at 0 never acts on a pair that is
+// composited (a pair just past the support by rounding gets f <= 0 and is
+// skipped as alpha < alpha_min).
 template <int KID>
 __device__ __forceinline__ void pair_alpha(float q, float o, const ParDev& P, float& D, float& xk, float& f,
                                            float& araw, float& alpha) {
   D = sqrt_approx(q);
   xk = __fmul_rn(D, P.inv_lambda);
-  f = kern_f<KID>(xk);
+  f = KID == LS_KERNEL_LINEAR ? __fmaf_rn(-D, P.inv_lambda, 1.f) : kern_f<KID>(xk);
   araw = __fmul_rn(o, f);
   alpha = fminf(P.alpha_max, araw);
 }
@@ -425,7 +435,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
       float s_e1 = 0.f, s_dx2 = 0.f, v5 = 0.f, v6 = 0.f, v7 = 0.f, v8 = 0.f;
       float s_q[RPT], s_dx[RPT];
       bool any = false;
-      const float kq = 0.5f * bb.y * P.inv_lambda;
+      const float kq = (KID == LS_KERNEL_LINEAR ? -0.5f : 0.5f) * bb.y * P.inv_lambda;
       // The per-pixel work is predicated rather than branched: once any lane
       // of the warp takes pixel slot p, every lane runs the same straight
       // line and a lane that does not take it contributes zeros.
@@ -441,9 +451,9 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
           bool take = row_in[r] && j < last[p] && q <= bb.z;
           if (!__any_sync(FULL, take)) continue;  // warp-uniform
           // a lane outside the support runs on finite stand-ins (q = 0 and
-          // zero offsets), so that its zero weights never meet an infinity
+          // e1 = 0; dx is a difference of two finite coordinates), so that
+          // its zero weights never meet an infinity
           const float qa = take ? q : 0.f;
-          dx = take ? dx : 0.f;
           e1 = take ? e1 : 0.f;
           float D, xk, f, araw, alpha;
           pair_alpha<KID>(qa, bb.y, P, D, xk, f, araw, alpha);
@@ -464,12 +474,15 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
           // a clamped alpha passes no gradient to o or D
           const float gat = (take && araw <= P.alpha_max) ? ga : 0.f;
           v5 += f * gat;
-          // dL/dq = dL/dalpha o f'(x) / (lambda 2 D), o / (2 lambda) per record
-          // (the linear profile's slope is -1 wherever alpha > 0)
-          float gD = (KID == LS_KERNEL_LINEAR ? -gat : gat * kern_df<KID>(xk)) * kq;
+          // dL/dq = dL/dalpha o f'(x) / (lambda 2 D); the record's factor
+          // o / (2 lambda) (and the linear profile's slope, -1 wherever
+          // alpha > 0) multiplies the sums once per entry, below.  1 / D from
+          // rsqrt(max(q, FLT_MIN)): exact where q is a normal number, and at
+          // the mean (q = 0) the huge gq meets dx = dy = e1 = 0
+          float gD = KID == LS_KERNEL_LINEAR ? gat : gat * kern_df<KID>(xk);
           if (AGS == 1) gD *= __expf(-D * D);
           else if (AGS == 2) gD *= __expf(-xk * xk);
-          const float gq = D > 0.f ? __fdividef(gD, D) : 0.f;
+          const float gq = gD * rsqrt_approx(fmaxf(qa, 1.17549435e-38f));
           const float gdx = gq * dx;
           s_e1 += gq * e1;
           s_dx[r] += gdx;
@@ -489,11 +502,11 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
         t3 += dy[r] * s_dx[r];
         t4 += dy[r] * dy[r] * s_q[r];
       }
-      v[0] = -2.f * a.z * s_e1;
-      v[1] = -2.f * t1;
-      v[2] = s_dx2;
-      v[3] = 2.f * t3;
-      v[4] = t4;
+      v[0] = -2.f * kq * a.z * s_e1;
+      v[1] = -2.f * kq * t1;
+      v[2] = kq * s_dx2;
+      v[3] = 2.f * kq * t3;
+      v[4] = kq * t4;
       v[5] = v5;
       v[6] = v6;
       v[7] = v7;

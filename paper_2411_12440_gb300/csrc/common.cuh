@@ -109,7 +109,6 @@ __device__ __forceinline__ float kern_support(int kid, float o, float amin) {
   }
 }
 
-// Launch helpers shared by the host-side launchers.
 // Programmatic dependent launch.  A kernel of the frame's chain is launched
 // with programmatic stream serialisation (launch_chain in kernels.h), so the
 // next kernel of the stream may be scheduled before this one has finished.
@@ -124,6 +123,7 @@ __device__ __forceinline__ void chain_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Launch helpers shared by the host-side launchers.
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace ls
