@@ -460,9 +460,13 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
           take = take && alpha >= P.alpha_min;
           any = any || take;
           const float4 cc = s_c[jj];
-          const float iom = __fdividef(1.f, 1.f - alpha);  // 1 - alpha >= 1 - alpha_max
+          // a lane that does not take the pair passes through it with alpha
+          // 0: its reciprocal is exactly 1 (the approximate reciprocal is
+          // exact at powers of two), so T and the weights need no select
+          const float at = take ? alpha : 0.f;
+          const float iom = __fdividef(1.f, 1.f - at);  // 1 - alpha >= 1 - alpha_max
           const float Tb = T[p] * iom;  // transmittance in front of this entry
-          const float wgt = take ? alpha * Tb : 0.f;
+          const float wgt = at * Tb;
           v6 += wgt * gC0[p];
           v7 += wgt * gC1[p];
           v8 += wgt * gC2[p];
@@ -470,7 +474,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ rec, const u
           const float gcd = gC0[p] * cc.x + gC1[p] * cc.y + gC2[p] * cc.z;
           const float ga = Tb * gcd - iom * GS[p];
           GS[p] += wgt * gcd;
-          T[p] = take ? Tb : T[p];
+          T[p] = Tb;
           // a clamped alpha passes no gradient to o or D
           const float gat = (take && araw <= P.alpha_max) ? ga : 0.f;
           v5 += f * gat;
