@@ -189,9 +189,20 @@ ls_status ls_project_bwd(int32_t n, const float* means, const float* scales, con
 /* Workspace of ls_render_bwd in bytes (the g2d buffer). */
 size_t ls_render_bwd_workspace(int64_t n_records);
 
+/* Workspace of ls_render_bwd with room behind the g2d buffer for a tile
+ * order of the given camera (bucket counts, buckets and order, 4 bytes per
+ * tile each); 0 for an invalid camera or parameters or n_records < 0. */
+size_t ls_render_bwd_workspace_ordered(int64_t n_records, const ls_camera* cam, const ls_params* params);
+
 /* a5+a6 in one call for one camera: zeroes a g2d buffer in `workspace`, runs
  * ls_blend_bwd then ls_project_bwd.  When g2d_out is not NULL the 2D
- * gradients are also copied there ([n][12] float). */
+ * gradients are also copied there ([n][12] float).  With ws_bytes at least
+ * ls_render_bwd_workspace_ordered(n, cam, params), the backward blend takes
+ * its tiles longest first: each tile's work is the largest n_last over its
+ * pixels, and two small kernels order the tiles by it (in quarter-octave
+ * buckets) so that the longest lists do not finish last.  The results are
+ * those of the plain order up to the order of the floating-point atomic
+ * additions into the 2D gradients. */
 ls_status ls_render_bwd(int32_t n, const float* means, const float* scales, const float* quats,
                         const float* opacities, const float* sh, const ls_camera* cam, const ls_params* params,
                         const void* proj, const int32_t* tile_ranges, const uint32_t* vals,

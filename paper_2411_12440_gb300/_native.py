@@ -71,6 +71,7 @@ PROTOTYPES = {
     "ls_blend_bwd": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ls_project_bwd": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _I32, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ls_render_bwd_workspace": (_SZ, [_I64]),
+    "ls_render_bwd_workspace_ordered": (_SZ, [_I64, _PC, _PP]),
     "ls_render_batch_workspace": (_SZ, [_I32, _PC, _I32, _PP, _I64]),
     "ls_mlp_forward": (_I32, [_I64, _P, ctypes.POINTER(LsMlp), _P, _P]),
     "ls_mlp_backward": (_I32, [_I64, _P, ctypes.POINTER(LsMlp), _P, ctypes.c_float, _P, _P, _P]),

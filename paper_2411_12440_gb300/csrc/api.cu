@@ -344,21 +344,60 @@ ls_status ls_render_stats(const void* proj, int64_t n_records, const ls_camera* 
   return LS_OK;
 }
 
-ls_status ls_blend_bwd(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
-                       const int32_t* tile_ranges, const uint32_t* vals, const float* t_final,
-                       const int32_t* n_last, const float* grad_image, const float* grad_t, float* g2d,
-                       int32_t* status_dev, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// ls_blend_bwd with an optional tile order (ls_render_bwd's ordered
+// workspace): `order_ws` holds the bucket counts, buckets and order of
+// launch_tile_order, the counts already zero.
+ls_status blend_bwd_impl(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                         const int32_t* tile_ranges, const uint32_t* vals, const float* t_final,
+                         const int32_t* n_last, const float* grad_image, const float* grad_t, float* g2d,
+                         char* order_ws, cudaStream_t st) {
   if (!params_ok(params) || n_records < 0) return LS_ERR_INVALID_ARG;
   CamTable T;
   if (!make_cams(cam, 1, params, T, nullptr)) return LS_ERR_INVALID_ARG;
   if (!tile_ranges || !t_final || !n_last || !grad_image) return LS_ERR_INVALID_ARG;
   if (n_records > 0 && (!proj || !vals || !g2d)) return LS_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(g2d) % 16) return LS_ERR_INVALID_ARG;
-  (void)status_dev;
+  const ParDev P = make_par(params);
+  const uint32_t* order = nullptr;
+  if (order_ws) {
+    const int64_t tiles = (int64_t)T.c[0].tiles_x * T.c[0].tiles_y;
+    unsigned* hist = reinterpret_cast<unsigned*>(order_ws);
+    uint32_t* bkt = reinterpret_cast<uint32_t*>(order_ws + al256(4 * (size_t)TILE_ORDER_BUCKETS));
+    uint32_t* ord = bkt + al256(4 * (size_t)tiles) / 4;
+    LS_TRY(launch_tile_order(n_last, T.c[0], P, hist, bkt, ord, st));
+    order = ord;
+  }
   ProjCPtr pp = proj_cplanes(proj, n_records);
-  LS_TRY(launch_blend_bwd(pp.rec, T.c[0], make_par(params), reinterpret_cast<const int2*>(tile_ranges), vals,
-                          t_final, n_last, grad_image, grad_t, g2d, static_cast<cudaStream_t>(stream)));
+  LS_TRY(launch_blend_bwd(pp.rec, T.c[0], P, reinterpret_cast<const int2*>(tile_ranges), vals, t_final, n_last,
+                          grad_image, grad_t, g2d, st, order));
   return LS_OK;
+}
+
+// Bytes of the tile-order part of an ordered backward workspace (0 when the
+// camera or the parameters are invalid).
+size_t order_ws_bytes(const ls_camera* cam, const ls_params* params) {
+  if (!params_ok(params)) return 0;
+  CamTable T;
+  if (!make_cams(cam, 1, params, T, nullptr)) return 0;
+  const size_t tiles = (size_t)T.c[0].tiles_x * T.c[0].tiles_y;
+  return al256(4 * (size_t)TILE_ORDER_BUCKETS) + 2 * al256(4 * tiles);
+}
+
+}  // namespace
+
+extern "C" {
+
+ls_status ls_blend_bwd(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                       const int32_t* tile_ranges, const uint32_t* vals, const float* t_final,
+                       const int32_t* n_last, const float* grad_image, const float* grad_t, float* g2d,
+                       int32_t* status_dev, void* stream) {
+  (void)status_dev;
+  return blend_bwd_impl(proj, n_records, cam, params, tile_ranges, vals, t_final, n_last, grad_image, grad_t, g2d,
+                        nullptr, static_cast<cudaStream_t>(stream));
 }
 
 ls_status ls_project_bwd(int32_t n, const float* means, const float* scales, const float* quats,
@@ -385,6 +424,11 @@ ls_status ls_project_bwd(int32_t n, const float* means, const float* scales, con
 
 size_t ls_render_bwd_workspace(int64_t n_records) { return n_records > 0 ? al256((size_t)n_records * 48) : 256; }
 
+size_t ls_render_bwd_workspace_ordered(int64_t n_records, const ls_camera* cam, const ls_params* params) {
+  const size_t o = order_ws_bytes(cam, params);
+  return n_records < 0 || o == 0 ? 0 : ls_render_bwd_workspace(n_records) + o;
+}
+
 ls_status ls_render_bwd(int32_t n, const float* means, const float* scales, const float* quats,
                         const float* opacities, const float* sh, const ls_camera* cam, const ls_params* params,
                         const void* proj, const int32_t* tile_ranges, const uint32_t* vals,
@@ -397,9 +441,14 @@ ls_status ls_render_bwd(int32_t n, const float* means, const float* scales, cons
   if (reinterpret_cast<uintptr_t>(workspace) % 256) return LS_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* g2d = static_cast<float*>(workspace);
-  if (n > 0) LS_TRY(cudaMemsetAsync(g2d, 0, (size_t)n * 48, st));
-  ls_status s = ls_blend_bwd(proj, n, cam, params, tile_ranges, vals, t_final, n_last, grad_image, grad_t, g2d,
-                             status_dev, stream);
+  // a workspace with room for the tile order blends the tiles longest first
+  const size_t plain = ls_render_bwd_workspace(n), ord = order_ws_bytes(cam, params);
+  char* order_ws = ord > 0 && ws_bytes >= plain + ord ? static_cast<char*>(workspace) + plain : nullptr;
+  // one clear for the 2D gradients and the order's bucket counts behind them
+  const size_t zero = order_ws ? plain + al256(4 * (size_t)TILE_ORDER_BUCKETS) : (size_t)n * 48;
+  if (zero > 0) LS_TRY(cudaMemsetAsync(g2d, 0, zero, st));
+  ls_status s = blend_bwd_impl(proj, n, cam, params, tile_ranges, vals, t_final, n_last, grad_image, grad_t, g2d,
+                               order_ws, st);
   if (s != LS_OK) return s;
   s = ls_project_bwd(n, means, scales, quats, opacities, sh, cam, 1, params, proj, g2d, g_means, g_scales, g_quats,
                      g_opac, g_sh, status_dev, stream);

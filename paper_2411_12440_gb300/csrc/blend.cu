@@ -551,14 +551,14 @@ __global__ void __launch_bounds__(128) blend_bwd_kernel(const float4* __restrict
                                                         const int32_t* __restrict__ n_last,
                                                         const float* __restrict__ grad_image,
                                                         const float* __restrict__ grad_t, float* __restrict__ g2d,
-                                                        int B) {
+                                                        int B, const uint32_t* __restrict__ order) {
   chain_enter();
   extern __shared__ float4 smem[];
   __shared__ int s_max;
   float* s_acc = reinterpret_cast<float*>(smem + 3 * B);
   uint32_t* s_id = reinterpret_cast<uint32_t*>(s_acc + 9 * B);
   int* s_touch = reinterpret_cast<int*>(s_id + B);
-  const int tile = blockIdx.x;
+  const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   TileJob J;
   J.x0 = (tile % cam.tiles_x) * P.tile_w;
   J.y0 = (tile / cam.tiles_x) * P.tile_h;
@@ -568,6 +568,56 @@ __global__ void __launch_bounds__(128) blend_bwd_kernel(const float4* __restrict
   J.pix_base = 0;
   bwd_tile<KID, AGS, PPR, RPT>(rec, vals, P, J, smem, smem + B, smem + 2 * B, s_acc, s_id, s_touch, &s_max, B, t_final,
                           n_last, grad_image, grad_t, g2d);
+}
+
+// ---------------------------------------------------------------- tile order
+// Bucket of a tile's work m (its largest n_last): 0 for none, else
+// 1 + 4 floor(log2 m) + the next two bits of m (quarter-octaves, 1..128).
+__device__ __forceinline__ int work_bucket(uint32_t m) {
+  if (m == 0) return 0;
+  const int l = 31 - __clz(m);
+  const int f = l >= 2 ? (int)((m >> (l - 2)) & 3u) : (int)((m << (2 - l)) & 3u);
+  return 1 + 4 * l + f;
+}
+
+// One warp per tile: the largest n_last over its pixels, bucketed.
+__global__ void __launch_bounds__(256) tile_work_kernel(const int32_t* __restrict__ n_last, const CamDev cam, int tw,
+                                                        int th, unsigned* hist, uint32_t* bkt) {
+  chain_enter();
+  const int tiles = cam.tiles_x * cam.tiles_y;
+  const int t = (int)blockIdx.x * 8 + ((int)threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= tiles) return;  // warp-uniform
+  const int x0 = (t % cam.tiles_x) * tw, y0 = (t / cam.tiles_x) * th;
+  int m = 0;
+  for (int i = lane; i < tw * th; i += 32) {
+    const int x = x0 + i % tw, y = y0 + i / tw;
+    if (x < cam.W && y < cam.H) m = max(m, n_last[(size_t)y * cam.W + x]);
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if (lane == 0) {
+    const int b = work_bucket((uint32_t)m);
+    bkt[t] = (uint32_t)b;
+    atomicAdd(&hist[b], 1u);
+  }
+}
+
+// One block: the buckets' offsets from the heaviest down, then every tile
+// placed in its bucket (in no particular order within it).
+__global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t* __restrict__ bkt, int tiles,
+                                                          const unsigned* __restrict__ hist,
+                                                          uint32_t* __restrict__ order) {
+  chain_enter();
+  __shared__ unsigned s_off[TILE_ORDER_BUCKETS];
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+    for (int b = TILE_ORDER_BUCKETS - 1; b >= 0; --b) {
+      s_off[b] = run;
+      run += hist[b];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) order[atomicAdd(&s_off[bkt[t]], 1u)] = (uint32_t)t;
 }
 
 // ---------------------------------------------------------------- batched
@@ -687,7 +737,8 @@ cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev&
 
 cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
                              const uint32_t* vals, const float* t_final, const int32_t* n_last,
-                             const float* grad_image, const float* grad_t, float* g2d, cudaStream_t st) {
+                             const float* grad_image, const float* grad_t, float* g2d, cudaStream_t st,
+                             const uint32_t* order) {
   // 4 pixels per row per thread; one row per thread (64 threads per 16x16
   // tile), 8x8 tiles: 2 pixels of one row
   const int ppr = P.tile_w * P.tile_h >= 256 ? 4 : 2;
@@ -699,7 +750,7 @@ cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev&
   cudaError_t e = cudaSuccess;
 #define LS_BB3(K, A, PR, RT)                                                                                  \
   e = launch_chain(blend_bwd_kernel<K, A, PR, RT>, dim3(grid), dim3(threads), sm, st, rec, cam, P, ranges, vals, \
-                   t_final, n_last, grad_image, grad_t, g2d, B)
+                   t_final, n_last, grad_image, grad_t, g2d, B, order)
 #define LS_BB2(K, A)                \
   do {                              \
     if (ppr == 4) LS_BB3(K, A, 4, 1); \
@@ -723,6 +774,17 @@ cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev&
 #undef LS_BB2
 #undef LS_BB3
   return e;
+}
+
+cudaError_t launch_tile_order(const int32_t* n_last, const CamDev& cam, const ParDev& P, unsigned* hist,
+                              uint32_t* bkt, uint32_t* order, cudaStream_t st) {
+  const int tiles = cam.tiles_x * cam.tiles_y;
+  if (tiles <= 0) return cudaSuccess;
+  const cudaError_t e = launch_chain(tile_work_kernel, dim3(ceil_div(tiles, 8)), dim3(256), 0, st, n_last, cam,
+                                     P.tile_w, P.tile_h, hist, bkt);
+  if (e != cudaSuccess) return e;
+  return launch_chain(tile_order_kernel, dim3(1), dim3(1024), 0, st, (const uint32_t*)bkt, tiles,
+                      (const unsigned*)hist, order);
 }
 
 }  // namespace ls

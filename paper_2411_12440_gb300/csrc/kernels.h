@@ -239,9 +239,20 @@ cudaError_t launch_blend_fwd(const float4* rec, const CamDev& cam, const ParDev&
 cudaError_t launch_blend_trunc(int mode, const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
                                const uint32_t* vals, float* image, float* t_final, int32_t* n_last,
                                const TruncArgs& ta, cudaStream_t st);
+// order != nullptr: CTA b blends tile order[b] (a permutation of the
+// camera's tiles, from launch_tile_order); else tile b.
 cudaError_t launch_blend_bwd(const float4* rec, const CamDev& cam, const ParDev& P, const int2* ranges,
                              const uint32_t* vals, const float* t_final, const int32_t* n_last,
-                             const float* grad_image, const float* grad_t, float* g2d, cudaStream_t st);
+                             const float* grad_image, const float* grad_t, float* g2d, cudaStream_t st,
+                             const uint32_t* order = nullptr);
+// Longest-first order of a camera's tiles for the backward blend: each
+// tile's work is the largest n_last over its pixels, bucketed by
+// quarter-octaves (TILE_ORDER_BUCKETS counts in `hist`, zero before the
+// call; `bkt` holds each tile's bucket), and `order` lists the tiles from
+// the heaviest bucket down.
+constexpr int TILE_ORDER_BUCKETS = 132;
+cudaError_t launch_tile_order(const int32_t* n_last, const CamDev& cam, const ParDev& P, unsigned* hist,
+                              uint32_t* bkt, uint32_t* order, cudaStream_t st);
 
 // ---- learned termination (learned.cu)
 struct DepthBins {

@@ -162,6 +162,8 @@ class Rasterizer:
         self.grow_margin = grow_margin
         self.capacity = 0
         self._bufs = {}
+        # ls_render_bwd blends the tiles longest first (ordered workspace)
+        self.bwd_tile_order = True
 
     # ---------------------------------------------------------------- buffers
     def _buf(self, name, nbytes, dtype=torch.uint8):
@@ -291,11 +293,15 @@ class Rasterizer:
                         quats=torch.empty_like(splats.quats), opac=torch.empty_like(splats.opac),
                         sh=torch.empty_like(splats.sh))
         g2d = torch.empty((n, 12), dtype=torch.float32, device=self.device) if want_g2d else None
-        wsb = N.lib().ls_render_bwd_workspace(n)
+        c, pc = cam_struct(cam), P.c()
+        wsb = 0
+        if self.bwd_tile_order:  # room for the longest-first tile order of the backward blend
+            wsb = N.lib().ls_render_bwd_workspace_ordered(n, ctypes.byref(c), ctypes.byref(pc))
+        wsb = wsb or N.lib().ls_render_bwd_workspace(n)
         ws = self._buf("bwd_ws", wsb + 256)
         ws_ptr = (ws.data_ptr() + 255) // 256 * 256
         N.check(N.lib().ls_render_bwd(n, _p(splats.means), _p(splats.scales), _p(splats.quats), _p(splats.opac),
-                                      _p(splats.sh), ctypes.byref(cam_struct(cam)), ctypes.byref(P.c()),
+                                      _p(splats.sh), ctypes.byref(c), ctypes.byref(pc),
                                       _p(state["proj"]), _p(state["ranges"]), _p(state["vals"]), _p(state["T"]),
                                       _p(state["n_last"]), _p(grad_image), _p(grad_T), _p(g["means"]),
                                       _p(g["scales"]), _p(g["quats"]), _p(g["opac"]), _p(g["sh"]), _p(g2d),

@@ -137,6 +137,18 @@ def test_debug_sort_wait_setter_checks_arguments(L):
     assert L.ls_debug_set_sort_wait(0, -1) == 0  # defaults again
 
 
+def test_ordered_backward_workspace_size(L):
+    from paper_2411_12440_gb300 import raster, scenes
+    cam = raster.cam_struct(scenes.identity_camera(100, 60))
+    good, odd = raster.RenderParams(), raster.RenderParams(tile_w=12, tile_h=12)
+    plain = L.ls_render_bwd_workspace(1000)
+    ordered = L.ls_render_bwd_workspace_ordered(1000, ctypes.byref(cam), ctypes.byref(good.c()))
+    tiles = 7 * 4  # 100 x 60 pixels in 16 x 16 tiles
+    assert ordered == plain + 768 + 2 * 256 and tiles * 4 <= 256
+    assert L.ls_render_bwd_workspace_ordered(1000, ctypes.byref(cam), ctypes.byref(odd.c())) == 0
+    assert L.ls_render_bwd_workspace_ordered(-1, ctypes.byref(cam), ctypes.byref(good.c())) == 0
+
+
 def test_dependent_launch_switch_checks_arguments(L):
     assert L.ls_set_dependent_launch(2) == 1 and L.ls_set_dependent_launch(-1) == 1
     assert L.ls_set_dependent_launch(0) == 0

@@ -10,6 +10,7 @@ import pytest
 import torch
 
 from paper_2411_12440_gb300 import raster, scenes
+from tests.gpu_helpers import log_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -117,3 +118,56 @@ def test_dependent_launch_gives_the_plain_launch_results():
     assert torch.equal(i0, i1) and torch.equal(t0, t1) and torch.equal(v0, v1) and torch.equal(r0, r1)
     for k in g0:
         assert _rel(g1[k], g0[k]) < 1e-5, k
+
+
+def _bucket(m):
+    """Quarter-octave bucket of a tile's work (its largest n_last)."""
+    if m == 0:
+        return 0
+    lg = int(m).bit_length() - 1
+    f = (m >> (lg - 2)) & 3 if lg >= 2 else (m << (2 - lg)) & 3
+    return 1 + 4 * lg + f
+
+
+def test_backward_tile_order_is_longest_first_and_changes_no_result():
+    """ls_render_bwd with the ordered workspace: the order it builds is a
+    permutation of the tiles, heaviest bucket first, each tile in the bucket
+    of its largest n_last; the gradients equal the plain order's up to the
+    order of the float atomics."""
+    sp, cam, gimg, gT = _setup(n=20_000, seed=11, W=333, H=250)
+    P = raster.RenderParams(sh_degree=3)
+    res = {}
+    for order in (False, True):
+        rz = raster.Rasterizer(P)
+        rz.bwd_tile_order = order
+        img, T, st = rz.forward(sp, cam)
+        g = rz.render_bwd(sp, cam, st, gimg, gT)
+        torch.cuda.synchronize()
+        rz.check_status("order %s" % order)
+        res[order] = (g, rz, st)
+    # float atomics add the per-tile contributions in another order; where a
+    # gradient cancels across tiles that shows as ~1e-4 relative at full size
+    rels = {k: _rel(res[True][0][k], res[False][0][k]) for k in res[False][0]}
+    log_parity("ordered_vs_plain_grad_rel_l2", **rels)
+    for k, r in rels.items():
+        assert r < 1e-3, k
+    g, rz, st = res[True]
+    tx, ty = (cam["width"] + 15) // 16, (cam["height"] + 15) // 16
+    tiles = tx * ty
+    n = sp.n
+    al = lambda b: (b + 255) // 256 * 256
+    ws = rz._bufs["bwd_ws"]
+    base = (ws.data_ptr() + 255) // 256 * 256 - ws.data_ptr()
+    raw = ws[base:].cpu().numpy()
+    o = al(n * 48) + al(4 * 132)
+    bkt = raw[o:o + 4 * tiles].view(np.uint32)
+    o += al(4 * tiles)
+    order = raw[o:o + 4 * tiles].view(np.uint32)
+    assert sorted(order.tolist()) == list(range(tiles))
+    nl = st["n_last"].cpu().numpy()
+    for t in range(tiles):
+        y0, x0 = (t // tx) * 16, (t % tx) * 16
+        assert bkt[t] == _bucket(int(nl[y0:y0 + 16, x0:x0 + 16].max())), t
+    seq = bkt[order]
+    assert np.all(seq[:-1] >= seq[1:])
+
