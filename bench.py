@@ -72,37 +72,52 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region:
+    one nvidia-smi process streaming a row every 50 ms, started (and its
+    first row awaited) before the region and ended after it."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=50):
         self.index = index
+        self.period_ms = period_ms
         self.rows = []
-        self._stop = threading.Event()
+        self._p = None
         self._t = None
+        self._first = threading.Event()
 
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
-                for line in out.stdout.strip().splitlines():
-                    self.rows.append([x.strip() for x in line.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+    def _read(self):
+        for line in self._p.stdout:
+            row = [x.strip() for x in line.split(",")]
+            if len(row) >= 9:
+                self.rows.append(row)
+                self._first.set()
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                        "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self._p = None
+            return self
+        self._t = threading.Thread(target=self._read, daemon=True)
         self._t.start()
+        self._first.wait(timeout=5.0)  # the first row: the clocks as the region starts
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=10)
+        if self._p is None:
+            return
+        self._p.terminate()  # our own child, by its handle
+        try:
+            self._p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self._p.kill()
+            self._p.wait(timeout=5)
+        self._t.join(timeout=5)
 
     def summary(self):
         sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
@@ -157,7 +172,7 @@ class Peaks:
         return sum(amount / (self.hbm * 1e9 if b == "hbm" else self.alu * 1e12) * 1e3 for b, amount in units)
 
 
-def frame_units(R, n_vis, K, n_eval, n_contrib, tiles, kp, sh_bytes=192):
+def frame_units(R, n_vis, K, n_eval, n_contrib, tiles, kp, sh_bytes=192, pixels=0):
     """Algorithmic work of each kernel of one frame: bytes for the
     HBM-bound stages, FP32 lane operations for the blends.  R records, n_vis
     visible, K tile keys, n_eval evaluated and n_contrib composited pairs."""
@@ -178,6 +193,8 @@ def frame_units(R, n_vis, K, n_eval, n_contrib, tiles, kp, sh_bytes=192):
         "project_bwd": ("hbm", (2 * (12 + par) + 48 + 4) * R),
         # 48 B per record cleared
         "g2d_clear": ("hbm", 48 * R),
+        # n_last read per pixel; a tile's bucket written and read, its order entry written
+        "tile_order": ("hbm", 4 * pixels + 12 * tiles),
     }
 
 
@@ -692,9 +709,10 @@ def main():
         return image, T, g
 
     # The same frame kernel by kernel, for the per-kernel durations of the
-    # rooflines: the adjoint as ls_blend_bwd into a cleared 2D-gradient buffer
-    # (cleared by a device copy through ls_copy) and ls_project_bwd.
-    kernel_names = ["project", "duplicate_sort", "blend_fwd", "g2d_clear", "blend_bwd", "project_bwd"]
+    # rooflines: the adjoint as ls_tile_order and ls_blend_bwd_ordered (the
+    # longest-first tile order ls_render_bwd uses) into a cleared 2D-gradient
+    # buffer (cleared by a device copy through ls_copy), then ls_project_bwd.
+    kernel_names = ["project", "duplicate_sort", "blend_fwd", "g2d_clear", "tile_order", "blend_bwd", "project_bwd"]
     g2d_zero = torch.zeros((R, 12), dtype=torch.float32, device=dev)
 
     def kernel_step(evs):
@@ -707,10 +725,12 @@ def main():
         evs[3].record()
         raster.copy_(g2d, g2d_zero)
         evs[4].record()
-        rz.blend_bwd(proj, R, cam, ranges, vals, T, n_last, gimg, gT, g2d)
+        order = rz.tile_order(cam, n_last)
         evs[5].record()
-        rz.project_bwd(sp, [cam], proj, g2d, out=gout)
+        rz.blend_bwd_ordered(proj, R, cam, ranges, order, vals, T, n_last, gimg, gT, g2d)
         evs[6].record()
+        rz.project_bwd(sp, [cam], proj, g2d, out=gout)
+        evs[7].record()
 
     # capacity from an exact count, then no host syncs inside steps
     proj, tc = rz.project(sp, [cam], counts=True)
@@ -951,7 +971,7 @@ def main():
     peaks = Peaks(dev)
     kp = 2
     nt = raster.tiles_of(cam, P)
-    units = frame_units(R, n_vis, K, n_eval, n_contrib, nt, kp, sh_bytes=192)
+    units = frame_units(R, n_vis, K, n_eval, n_contrib, nt, kp, sh_bytes=192, pixels=H * W)
     stage_roofs = {k: peaks.entry(*units[k], kernel_ms[k]) for k in kernel_names}
     # the dominant kernel: the longest stage that is one launch (duplicate_sort
     # is a chain of a dozen launches, none of them longer than the blends)
@@ -995,8 +1015,9 @@ def main():
             "roofline": roof, "clocks": clocks.summary(), "clocks_kernel_by_kernel": kclocks.summary(), "e2e": e2e,
             # per step: ls_project 1; ls_duplicate_sort 13 + kp (depth histogram, scan, 4 depth passes, boxes,
             # key count, 2-launch warp-count scan, key copy, digit scan, kp tile passes, ranges); ls_render_fwd
-            # 1; ls_render_bwd 2 (blend adjoint, projection adjoint; its clear is a memset)
-            "gpu_launches": args.steps * (1 + (13 + kp) + 1 + 2)}
+            # 1; ls_render_bwd 4 (tile work, tile order, blend adjoint, projection adjoint; its clear is a
+            # memset)
+            "gpu_launches": args.steps * (1 + (13 + kp) + 1 + 4)}
 
     if not args.no_batch and args.prims is None:
         line["batched"] = bench_batched(dev)

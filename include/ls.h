@@ -186,6 +186,27 @@ ls_status ls_project_bwd(int32_t n, const float* means, const float* scales, con
                          float* g_scales, float* g_quats, float* g_opac, float* g_sh, int32_t* status_dev,
                          void* stream);
 
+/* Longest-first order of a camera's tiles for the backward blend (the
+ * order ls_render_bwd uses with its ordered workspace): each tile's work is
+ * the largest n_last over its pixels (n_last [H][W] as written by
+ * ls_render_fwd), the tiles go into quarter-octave buckets of it and
+ * tile_order [tiles_x * tiles_y] (caller-owned, device) lists them from the
+ * heaviest bucket down, in no particular order within a bucket.  workspace:
+ * device scratch of at least ls_tile_order_workspace bytes, 256-byte
+ * aligned.  LS_ERR_INVALID_ARG for an invalid camera or parameters, null
+ * pointers or a short workspace. */
+size_t ls_tile_order_workspace(const ls_camera* cam, const ls_params* params);
+ls_status ls_tile_order(const int32_t* n_last, const ls_camera* cam, const ls_params* params, uint32_t* tile_order,
+                        void* workspace, size_t ws_bytes, void* stream);
+
+/* ls_blend_bwd with CTA b blending tile tile_order[b] (a permutation of the
+ * camera's tiles, e.g. from ls_tile_order; not NULL).  Results as
+ * ls_blend_bwd up to the order of the floating-point atomic additions. */
+ls_status ls_blend_bwd_ordered(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                               const int32_t* tile_ranges, const uint32_t* tile_order, const uint32_t* vals,
+                               const float* t_final, const int32_t* n_last, const float* grad_image,
+                               const float* grad_t, float* g2d, int32_t* status_dev, void* stream);
+
 /* Workspace of ls_render_bwd in bytes (the g2d buffer). */
 size_t ls_render_bwd_workspace(int64_t n_records);
 

@@ -69,6 +69,9 @@ PROTOTYPES = {
     "ls_tile_features": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _SZ, _P]),
     "ls_render_learned_workspace": (_SZ, [_I32, _PC, _PP, _I64]),
     "ls_blend_bwd": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ls_tile_order_workspace": (_SZ, [_PC, _PP]),
+    "ls_tile_order": (_I32, [_P, _PC, _PP, _P, _P, _SZ, _P]),
+    "ls_blend_bwd_ordered": (_I32, [_P, _I64, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ls_project_bwd": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _I32, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ls_render_bwd_workspace": (_SZ, [_I64]),
     "ls_render_bwd_workspace_ordered": (_SZ, [_I64, _PC, _PP]),

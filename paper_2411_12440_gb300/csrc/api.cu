@@ -348,43 +348,53 @@ ls_status ls_render_stats(const void* proj, int64_t n_records, const ls_camera* 
 
 namespace {
 
-// ls_blend_bwd with an optional tile order (ls_render_bwd's ordered
-// workspace): `order_ws` holds the bucket counts, buckets and order of
-// launch_tile_order, the counts already zero.
+// ls_blend_bwd with an optional tile order (CTA b blends tile order[b]).
 ls_status blend_bwd_impl(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
                          const int32_t* tile_ranges, const uint32_t* vals, const float* t_final,
                          const int32_t* n_last, const float* grad_image, const float* grad_t, float* g2d,
-                         char* order_ws, cudaStream_t st) {
+                         const uint32_t* order, cudaStream_t st) {
   if (!params_ok(params) || n_records < 0) return LS_ERR_INVALID_ARG;
   CamTable T;
   if (!make_cams(cam, 1, params, T, nullptr)) return LS_ERR_INVALID_ARG;
   if (!tile_ranges || !t_final || !n_last || !grad_image) return LS_ERR_INVALID_ARG;
   if (n_records > 0 && (!proj || !vals || !g2d)) return LS_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(g2d) % 16) return LS_ERR_INVALID_ARG;
-  const ParDev P = make_par(params);
-  const uint32_t* order = nullptr;
-  if (order_ws) {
-    const int64_t tiles = (int64_t)T.c[0].tiles_x * T.c[0].tiles_y;
-    unsigned* hist = reinterpret_cast<unsigned*>(order_ws);
-    uint32_t* bkt = reinterpret_cast<uint32_t*>(order_ws + al256(4 * (size_t)TILE_ORDER_BUCKETS));
-    uint32_t* ord = bkt + al256(4 * (size_t)tiles) / 4;
-    LS_TRY(launch_tile_order(n_last, T.c[0], P, hist, bkt, ord, st));
-    order = ord;
-  }
   ProjCPtr pp = proj_cplanes(proj, n_records);
-  LS_TRY(launch_blend_bwd(pp.rec, T.c[0], P, reinterpret_cast<const int2*>(tile_ranges), vals, t_final, n_last,
-                          grad_image, grad_t, g2d, st, order));
+  LS_TRY(launch_blend_bwd(pp.rec, T.c[0], make_par(params), reinterpret_cast<const int2*>(tile_ranges), vals,
+                          t_final, n_last, grad_image, grad_t, g2d, st, order));
   return LS_OK;
 }
 
-// Bytes of the tile-order part of an ordered backward workspace (0 when the
-// camera or the parameters are invalid).
-size_t order_ws_bytes(const ls_camera* cam, const ls_params* params) {
+// Tiles of a valid single camera, else 0.
+int64_t cam_tiles(const ls_camera* cam, const ls_params* params, CamTable* out = nullptr) {
   if (!params_ok(params)) return 0;
   CamTable T;
   if (!make_cams(cam, 1, params, T, nullptr)) return 0;
-  const size_t tiles = (size_t)T.c[0].tiles_x * T.c[0].tiles_y;
-  return al256(4 * (size_t)TILE_ORDER_BUCKETS) + 2 * al256(4 * tiles);
+  if (out) *out = T;
+  return (int64_t)T.c[0].tiles_x * T.c[0].tiles_y;
+}
+
+// Scratch of a tile order: bucket counts, then each tile's bucket.
+size_t order_scratch_bytes(int64_t tiles) { return al256(4 * (size_t)TILE_ORDER_BUCKETS) + al256(4 * (size_t)tiles); }
+
+// The longest-first order of the camera's tiles into `order` (launch_tile_order);
+// `scratch` holds order_scratch_bytes, its bucket counts already zero.
+ls_status tile_order_impl(const int32_t* n_last, const ls_camera* cam, const ls_params* params, uint32_t* order,
+                          char* scratch, cudaStream_t st) {
+  CamTable T;
+  const int64_t tiles = cam_tiles(cam, params, &T);
+  if (tiles == 0 || !n_last || !order || !scratch) return LS_ERR_INVALID_ARG;
+  unsigned* hist = reinterpret_cast<unsigned*>(scratch);
+  uint32_t* bkt = reinterpret_cast<uint32_t*>(scratch + al256(4 * (size_t)TILE_ORDER_BUCKETS));
+  LS_TRY(launch_tile_order(n_last, T.c[0], make_par(params), hist, bkt, order, st));
+  return LS_OK;
+}
+
+// Bytes of the tile-order part of an ordered backward workspace (scratch and
+// the order; 0 when the camera or the parameters are invalid).
+size_t order_ws_bytes(const ls_camera* cam, const ls_params* params) {
+  const int64_t tiles = cam_tiles(cam, params);
+  return tiles == 0 ? 0 : order_scratch_bytes(tiles) + al256(4 * (size_t)tiles);
 }
 
 }  // namespace
@@ -398,6 +408,31 @@ ls_status ls_blend_bwd(const void* proj, int64_t n_records, const ls_camera* cam
   (void)status_dev;
   return blend_bwd_impl(proj, n_records, cam, params, tile_ranges, vals, t_final, n_last, grad_image, grad_t, g2d,
                         nullptr, static_cast<cudaStream_t>(stream));
+}
+
+size_t ls_tile_order_workspace(const ls_camera* cam, const ls_params* params) {
+  const int64_t tiles = cam_tiles(cam, params);
+  return tiles == 0 ? 0 : order_scratch_bytes(tiles);
+}
+
+ls_status ls_tile_order(const int32_t* n_last, const ls_camera* cam, const ls_params* params, uint32_t* tile_order,
+                        void* workspace, size_t ws_bytes, void* stream) {
+  const size_t need = ls_tile_order_workspace(cam, params);
+  if (need == 0 || !workspace || ws_bytes < need || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return LS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LS_TRY(cudaMemsetAsync(workspace, 0, 4 * (size_t)TILE_ORDER_BUCKETS, st));
+  return tile_order_impl(n_last, cam, params, tile_order, static_cast<char*>(workspace), st);
+}
+
+ls_status ls_blend_bwd_ordered(const void* proj, int64_t n_records, const ls_camera* cam, const ls_params* params,
+                               const int32_t* tile_ranges, const uint32_t* tile_order, const uint32_t* vals,
+                               const float* t_final, const int32_t* n_last, const float* grad_image,
+                               const float* grad_t, float* g2d, int32_t* status_dev, void* stream) {
+  (void)status_dev;
+  if (!tile_order) return LS_ERR_INVALID_ARG;
+  return blend_bwd_impl(proj, n_records, cam, params, tile_ranges, vals, t_final, n_last, grad_image, grad_t, g2d,
+                        tile_order, static_cast<cudaStream_t>(stream));
 }
 
 ls_status ls_project_bwd(int32_t n, const float* means, const float* scales, const float* quats,
@@ -447,8 +482,15 @@ ls_status ls_render_bwd(int32_t n, const float* means, const float* scales, cons
   // one clear for the 2D gradients and the order's bucket counts behind them
   const size_t zero = order_ws ? plain + al256(4 * (size_t)TILE_ORDER_BUCKETS) : (size_t)n * 48;
   if (zero > 0) LS_TRY(cudaMemsetAsync(g2d, 0, zero, st));
+  const uint32_t* order = nullptr;
+  if (order_ws) {
+    uint32_t* ord = reinterpret_cast<uint32_t*>(order_ws + order_scratch_bytes(cam_tiles(cam, params)));
+    const ls_status so = tile_order_impl(n_last, cam, params, ord, order_ws, st);
+    if (so != LS_OK) return so;
+    order = ord;
+  }
   ls_status s = blend_bwd_impl(proj, n, cam, params, tile_ranges, vals, t_final, n_last, grad_image, grad_t, g2d,
-                               order_ws, st);
+                               order, st);
   if (s != LS_OK) return s;
   s = ls_project_bwd(n, means, scales, quats, opacities, sh, cam, 1, params, proj, g2d, g_means, g_scales, g_quats,
                      g_opac, g_sh, status_dev, stream);

@@ -269,6 +269,24 @@ class Rasterizer:
                                      _p(ranges), _p(vals), _p(T), _p(n_last), _p(grad_image), _p(grad_T), _p(g2d),
                                      _p(self.status), _stream()), "ls_blend_bwd")
 
+    def tile_order(self, cam, n_last):
+        """Longest-first order of the camera's tiles for the backward blend
+        (ls_tile_order): uint32 [tiles]."""
+        c, pc = cam_struct(cam), self.params.c()
+        order = torch.empty(tiles_of(cam, self.params), dtype=torch.int32, device=self.device)
+        wsb = N.lib().ls_tile_order_workspace(ctypes.byref(c), ctypes.byref(pc))
+        ws = self._buf("order_ws", wsb + 256)
+        ws_ptr = (ws.data_ptr() + 255) // 256 * 256
+        N.check(N.lib().ls_tile_order(_p(n_last), ctypes.byref(c), ctypes.byref(pc), _p(order), ctypes.c_void_p(ws_ptr),
+                                      wsb, _stream()), "ls_tile_order")
+        return order
+
+    def blend_bwd_ordered(self, proj, R, cam, ranges, order, vals, T, n_last, grad_image, grad_T, g2d):
+        """a5 alone with tile b of the launch = order[b] (ls_blend_bwd_ordered)."""
+        N.check(N.lib().ls_blend_bwd_ordered(_p(proj), R, ctypes.byref(cam_struct(cam)), ctypes.byref(self.params.c()),
+                                             _p(ranges), _p(order), _p(vals), _p(T), _p(n_last), _p(grad_image),
+                                             _p(grad_T), _p(g2d), _p(self.status), _stream()), "ls_blend_bwd_ordered")
+
     def project_bwd(self, splats: Splats, cams, proj, g2d, out=None):
         """a6 alone: 3D gradients from g2d (overwritten into `out` when given)."""
         g = out or dict(means=torch.empty_like(splats.means), scales=torch.empty_like(splats.scales),

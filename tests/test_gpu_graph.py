@@ -171,3 +171,30 @@ def test_backward_tile_order_is_longest_first_and_changes_no_result():
     seq = bkt[order]
     assert np.all(seq[:-1] >= seq[1:])
 
+
+
+def test_tile_order_entry_points():
+    """ls_tile_order lists every tile once, heaviest bucket first (buckets of
+    the largest n_last recomputed here); ls_blend_bwd_ordered with it gives
+    ls_blend_bwd's 2D gradients up to the order of the float atomics."""
+    sp, cam, gimg, gT = _setup(n=15_000, seed=13, W=300, H=200)
+    P = raster.RenderParams(sh_degree=3)
+    rz = raster.Rasterizer(P)
+    img, T, st = rz.forward(sp, cam)
+    order = rz.tile_order(cam, st["n_last"])
+    g_plain = torch.zeros((sp.n, 12), dtype=torch.float32, device="cuda")
+    g_ord = torch.zeros_like(g_plain)
+    rz.blend_bwd(st["proj"], sp.n, cam, st["ranges"], st["vals"], T, st["n_last"], gimg, gT, g_plain)
+    rz.blend_bwd_ordered(st["proj"], sp.n, cam, st["ranges"], order, st["vals"], T, st["n_last"], gimg, gT, g_ord)
+    torch.cuda.synchronize()
+    rz.check_status("ordered entry points")
+    tx, ty = (cam["width"] + 15) // 16, (cam["height"] + 15) // 16
+    o = order.cpu().numpy().astype(np.int64)
+    assert sorted(o.tolist()) == list(range(tx * ty))
+    nl = st["n_last"].cpu().numpy()
+    b = np.array([_bucket(int(nl[(t // tx) * 16:(t // tx) * 16 + 16, (t % tx) * 16:(t % tx) * 16 + 16].max()))
+                  for t in o])
+    assert np.all(b[:-1] >= b[1:])
+    r = _rel(g_ord, g_plain)
+    log_parity("ordered_vs_plain_g2d_rel_l2", g2d=r)
+    assert r < 1e-4
