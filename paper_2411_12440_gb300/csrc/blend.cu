@@ -608,16 +608,17 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint32_t* __rest
                                                           const unsigned* __restrict__ hist,
                                                           uint32_t* __restrict__ order) {
   chain_enter();
-  __shared__ unsigned s_off[TILE_ORDER_BUCKETS];
-  if (threadIdx.x == 0) {
+  __shared__ unsigned s_cnt[TILE_ORDER_BUCKETS], s_off[TILE_ORDER_BUCKETS];
+  const int tid = threadIdx.x;
+  if (tid < TILE_ORDER_BUCKETS) s_cnt[tid] = hist[tid];
+  __syncthreads();
+  if (tid < TILE_ORDER_BUCKETS) {  // tiles in heavier buckets come first
     unsigned run = 0;
-    for (int b = TILE_ORDER_BUCKETS - 1; b >= 0; --b) {
-      s_off[b] = run;
-      run += hist[b];
-    }
+    for (int b = TILE_ORDER_BUCKETS - 1; b > tid; --b) run += s_cnt[b];
+    s_off[tid] = run;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < tiles; t += blockDim.x) order[atomicAdd(&s_off[bkt[t]], 1u)] = (uint32_t)t;
+  for (int t = tid; t < tiles; t += blockDim.x) order[atomicAdd(&s_off[bkt[t]], 1u)] = (uint32_t)t;
 }
 
 // ---------------------------------------------------------------- batched
