@@ -74,11 +74,14 @@ cudaError_t launch_project_bwd(int n, const float* means, const float* scales, c
                                float* g_opac, float* g_sh, cudaStream_t st);
 
 // ---- onesweep radix sort (sort.cu)
-constexpr int SORT_THREADS = 256;
-// Keys per thread of a partition: 4608-key partitions take 55 KB of shared
-// memory, so four CTAs still fit an SM.  On the bench frame 8, 11, 13, 15, 16
-// and 17 were slower (more partitions to look back over), 19 and 24 too
-// (three CTAs per SM).
+// Threads of a onesweep CTA: two CTAs of 512 per SM (0.599 ms for the
+// duplicate + sort stage of the 3M-primitive 1080p frame, against 0.605 for
+// four of 256 and 0.657 for one of 1024).
+constexpr int SORT_THREADS = 512;
+// Keys per thread of a partition: 9216-key partitions take 110 KB of shared
+// memory, so two CTAs still fit an SM.  With 256-thread CTAs, 8, 11, 13,
+// 15, 16 and 17 were slower on the bench frame (more partitions to look back
+// over), 19 and 24 too (three CTAs per SM).
 constexpr int SORT_ITEMS = 18;
 constexpr int SORT_PART = SORT_THREADS * SORT_ITEMS;  // keys per partition
 constexpr int RADIX = 256;

@@ -28,13 +28,16 @@ constexpr uint64_t LB_VAL = (1ull << 62) - 1;
 constexpr int SPIN_LIMIT_DEFAULT = 1 << 21;
 int g_spin_limit = SPIN_LIMIT_DEFAULT;
 int g_hold_part = -1;
-constexpr int SORT_WARPS = SORT_THREADS / 32;
+// Threads of a onesweep CTA, its warps and the CTAs an SM holds.
+constexpr int OS_THREADS = SORT_THREADS;
+constexpr int SORT_WARPS = OS_THREADS / 32;
+constexpr int OS_CTAS_PER_SM = 1024 / OS_THREADS;
 // Predecessor states a look-back step loads at once.  On the 3M-primitive
 // 1080p frame a partition's look-back reads 15-33 predecessors and is
 // its longest phase; 4 at once took 4 us off the duplicate + sort stage,
 // 8 and 16 added 10 and 37 us (more polling traffic).
 constexpr int LB_WINDOW = 4;
-static_assert(SORT_THREADS == RADIX, "one thread per digit");
+static_assert(OS_THREADS >= RADIX && OS_THREADS % RADIX == 0, "a thread for every digit");
 
 __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
   uint64_t v;
@@ -45,7 +48,8 @@ __device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Inclusive scan of one value per thread over a block of SORT_THREADS.
+// Inclusive scan of one value per thread over a block of WARPS warps.
+template <int WARPS>
 __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t* s_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -56,13 +60,13 @@ __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t* s_warp
   if (lane == 31) s_warp[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    uint32_t w = lane < SORT_WARPS ? s_warp[lane] : 0;
+    uint32_t w = lane < WARPS ? s_warp[lane] : 0;
 #pragma unroll
-    for (int o = 1; o < SORT_WARPS; o <<= 1) {
+    for (int o = 1; o < WARPS; o <<= 1) {
       uint32_t u = __shfl_up_sync(0xffffffffu, w, o);
       if (lane >= o) w += u;
     }
-    if (lane < SORT_WARPS) s_warp[lane] = w;
+    if (lane < WARPS) s_warp[lane] = w;
   }
   __syncthreads();
   return v + (warp > 0 ? s_warp[warp - 1] : 0);
@@ -89,10 +93,10 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t* __restr
 
 __global__ void __launch_bounds__(RADIX) radix_scan_kernel(uint32_t* hist) {
   chain_enter();
-  __shared__ uint32_t s_warp[SORT_WARPS];
+  __shared__ uint32_t s_warp[RADIX / 32];
   uint32_t* h = hist + (size_t)blockIdx.x * RADIX;
   uint32_t v = h[threadIdx.x];
-  uint32_t incl = block_incl_scan(v, s_warp);
+  uint32_t incl = block_incl_scan<RADIX / 32>(v, s_warp);
   h[threadIdx.x] = incl - v;
 }
 
@@ -116,16 +120,16 @@ struct OnesweepSmem {
 };
 
 // BITS: digit width of the pass (<= 8); digits are (key >> shift) & (2^BITS - 1).
-// ITEMS: keys per thread; a partition holds SORT_THREADS * ITEMS keys.
+// ITEMS: keys per thread; a partition holds OS_THREADS * ITEMS keys.
 template <int BITS, int ITEMS>
-__global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
+__global__ void __launch_bounds__(OS_THREADS, OS_CTAS_PER_SM) onesweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const int64_t* n_dev, int64_t n_host, int shift,
     const uint32_t* __restrict__ digit_base, uint64_t* lookback, uint32_t* part_ctr, uint2* ranges,
     int32_t* status, int spin_limit, int hold_part) {
   chain_enter();
   constexpr uint32_t MASK = (1u << BITS) - 1u;
-  constexpr int PART = SORT_THREADS * ITEMS;
+  constexpr int PART = OS_THREADS * ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   OnesweepSmem<PART>& S = *reinterpret_cast<OnesweepSmem<PART>*>(smem_raw);
 
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
   // persistent: the block takes partitions by ticket until none is left
   for (;;) {
   __syncthreads();  // the previous partition is done with shared memory
-  for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&S.whist[0][0])[i] = 0;
+  for (int i = tid; i < SORT_WARPS * RADIX; i += OS_THREADS) (&S.whist[0][0])[i] = 0;
   if (tid == 0) S.part = atomicAdd(part_ctr, 1u);
   __syncthreads();
   const uint32_t part = S.part;
@@ -144,7 +148,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
 
   // values: asynchronous copy into shared memory, in flight during ranking
   if (vals_in) {
-    for (int i = tid; i < n_in; i += SORT_THREADS) cp_async4(&S.vin[i], vals_in + base + i);
+    for (int i = tid; i < n_in; i += OS_THREADS) cp_async4(&S.vin[i], vals_in + base + i);
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
   // keys: warp-striped, warp w holds positions w*32*ITEMS + i*32 + lane
@@ -180,22 +184,26 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
   }
   __syncthreads();
 
-  // one thread per digit: warp-exclusive offsets, block count, look-back
+  // one thread per digit (the first RADIX threads): warp-exclusive offsets,
+  // block count, look-back
   {
     const int d = tid;
+    const bool digit = d < RADIX;
     uint32_t run = 0;
+    if (digit) {
 #pragma unroll
-    for (int w = 0; w < SORT_WARPS; ++w) {
-      uint32_t c = S.whist[w][d];
-      S.whist[w][d] = run;
-      run += c;
+      for (int w = 0; w < SORT_WARPS; ++w) {
+        uint32_t c = S.whist[w][d];
+        S.whist[w][d] = run;
+        run += c;
+      }
     }
     uint64_t* my = lookback + (size_t)part * RADIX + d;
-    const bool used = d <= (int)MASK;  // digits beyond the pass's width never occur
+    const bool used = digit && d <= (int)MASK;  // digits beyond the pass's width never occur
     const bool publish = (int)part != hold_part;
     if (used && publish) st_relaxed_u64(my, (part == 0 ? LB_INC : LB_AGG) | (uint64_t)run);
-    const uint32_t incl = block_incl_scan(run, S.warp);
-    S.local[d] = incl - run;
+    const uint32_t incl = block_incl_scan<SORT_WARPS>(run, S.warp);  // threads past RADIX add 0
+    if (digit) S.local[d] = incl - run;
     uint64_t prefix = 0;
     if (used && part > 0) {
       // Walk back over the predecessors LB_WINDOW at a time (their states
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
       }
       if (publish) st_relaxed_u64(my, LB_INC | (prefix + run));
     }
-    S.glob[d] = digit_base[d] + (uint32_t)prefix - S.local[d];
+    if (digit) S.glob[d] = digit_base[d] + (uint32_t)prefix - S.local[d];
   }
   __syncthreads();
 
@@ -253,7 +261,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) onesweep_kernel(
   if (vals_in) cp_async_wait_all();
   __syncthreads();
   // digit runs go to consecutive global positions
-  for (int s = tid; s < n_in; s += SORT_THREADS) {
+  for (int s = tid; s < n_in; s += OS_THREADS) {
     const uint32_t key = S.keys[s];
     const uint32_t dst = S.glob[(key >> shift) & MASK] + (uint32_t)s;
     if (dst < (uint64_t)n) {
@@ -285,7 +293,7 @@ inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 }  // namespace
 
 size_t sort_scratch_bytes(int64_t cap, int passes, int items) {
-  const int64_t part = (int64_t)SORT_THREADS * items;
+  const int64_t part = (int64_t)OS_THREADS * items;
   int64_t parts = cap > 0 ? (cap + part - 1) / part : 1;
   return al256((size_t)passes * RADIX * 4) + al256((size_t)passes * 4) +
          al256((size_t)passes * parts * RADIX * 8);
@@ -293,7 +301,7 @@ size_t sort_scratch_bytes(int64_t cap, int passes, int items) {
 
 SortScratch sort_scratch_carve(void* base, int64_t cap, int passes, int items) {
   SortScratch s;
-  const int64_t part = (int64_t)SORT_THREADS * items;
+  const int64_t part = (int64_t)OS_THREADS * items;
   s.items = items;
   s.parts = cap > 0 ? (cap + part - 1) / part : 1;
   char* p = static_cast<char*>(base);
@@ -324,7 +332,7 @@ static cudaError_t onesweep_launch(const uint32_t* keys_in, const uint32_t* vals
                                    int pass, const SortScratch& s, int32_t* ranges, int32_t* status, cudaStream_t st) {
   // the dynamic shared memory limit is a per-device attribute of the kernel
   static bool attr_set[64] = {false};
-  constexpr int PART = SORT_THREADS * ITEMS;
+  constexpr int PART = OS_THREADS * ITEMS;
   const size_t sm = sizeof(OnesweepSmem<PART>);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -340,9 +348,9 @@ static cudaError_t onesweep_launch(const uint32_t* keys_in, const uint32_t* vals
   e = current_sm_count(&sms);
   if (e != cudaSuccess) return e;
   const int64_t parts = (cap > 0 ? cap + PART - 1 : PART) / PART;
-  const int64_t resident = (int64_t)sms * 4;
+  const int64_t resident = (int64_t)sms * OS_CTAS_PER_SM;
   const unsigned grid = (unsigned)(parts < resident ? parts : resident);
-  return launch_chain(onesweep_kernel<BITS, ITEMS>, dim3(grid), dim3(SORT_THREADS), sm, st, keys_in, vals_in, keys_out,
+  return launch_chain(onesweep_kernel<BITS, ITEMS>, dim3(grid), dim3(OS_THREADS), sm, st, keys_in, vals_in, keys_out,
                       vals_out, n_dev, n_host, shift, (const uint32_t*)(s.hist + (size_t)pass * RADIX),
                       s.lookback + (size_t)pass * s.parts * RADIX, s.part_ctr + pass,
                       reinterpret_cast<uint2*>(ranges), status, g_spin_limit, ranges ? g_hold_part : -1);
