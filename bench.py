@@ -973,9 +973,10 @@ def main():
     nt = raster.tiles_of(cam, P)
     units = frame_units(R, n_vis, K, n_eval, n_contrib, nt, kp, sh_bytes=192, pixels=H * W)
     stage_roofs = {k: peaks.entry(*units[k], kernel_ms[k]) for k in kernel_names}
-    # the dominant kernel: the longest stage that is one launch (duplicate_sort
-    # is a chain of a dozen launches, none of them longer than the blends)
-    dom = max((k for k in kernel_ms if k not in ("duplicate_sort", "g2d_clear")), key=lambda k: kernel_ms[k])
+    # the dominant kernel: the longest of the stages that are one launch
+    # each (duplicate_sort is a chain of a dozen launches, none of them
+    # longer than the blends; the clear and the tile order are small helpers)
+    dom = max(("project", "blend_fwd", "blend_bwd", "project_bwd"), key=lambda k: kernel_ms[k])
     roof = dict(stage_roofs[dom])
     if roof["bound"] == "alu":
         roof["peak_check"] = {"measured_fma_tops": round(peaks.fma_probe, 3),
