@@ -35,7 +35,7 @@ LANES_PER_SM = 128
 # DRAM traffic per launch of the dominant kernel from one ncu capture of the
 # bench workload (dram__bytes_read.sum + dram__bytes_write.sum), valid only
 # while the kernel source is the one measured (sha1 prefix of the file).
-NCU_TRAFFIC = {"blend_bwd": {"bytes": 71540736 + 1596672, "src": "03e12f742e33"}}
+NCU_TRAFFIC = {"blend_bwd": {"bytes": 71584512 + 1875200, "src": "f92c872d9558"}}
 
 
 def _src_hash(name):
