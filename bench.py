@@ -996,9 +996,9 @@ def main():
     # six 8-bit passes over 12-byte (tile | depth, id) keys at 24 B per key
     # per pass plus an 8 B histogram read): what that method would move for
     # the same K, over the time this design takes
-    survey_bytes = 12 * K + 8 * R + (24 * 6 + 8) * K
+    classic_bytes = 12 * K + 8 * R + (24 * 6 + 8) * K
     stage_roofs["duplicate_sort"]["frac_classic_method_bytes"] = round(
-        survey_bytes / (kernel_ms["duplicate_sort"] * 1e-3) / 1e9 / peaks.hbm, 4)
+        classic_bytes / (kernel_ms["duplicate_sort"] * 1e-3) / 1e9 / peaks.hbm, 4)
 
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
