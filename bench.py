@@ -362,13 +362,26 @@ def bench_batched(dev, reps=10):
     br.check()
     ms_batch = e0.elapsed_time(e1) / reps
     K = int(br.n_keys.item())
-    del br
+    # the blending stage alone, on what the last call left in the workspace
+    imgs = br.images.clone()
+    br.blend_only()
+    torch.cuda.synchronize(dev)
+    br.check()
+    assert torch.equal(br.images, imgs), "blend-only images differ"
+    e0.record()
+    for _ in range(reps):
+        br.blend_only()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms_blend = e0.elapsed_time(e1) / reps
+    del br, imgs
     torch.cuda.empty_cache()
     # Roofline of the batched call: its projection and duplicate/sort stages
     # timed through ls_project / ls_duplicate_sort on the same 64 cameras and
-    # tile shape; the persistent blend (with its job queue) is the rest of the
-    # call.  Blend work from the per-camera counting forward (the batched
-    # blend walks the same lists with the same per-tile code).
+    # tile shape; the persistent blend (with its job queue) timed alone
+    # through ls_render_batch_blend.  Blend work from the per-camera counting
+    # forward (the batched blend walks the same lists with the same per-tile
+    # code).
     rzb = raster.Rasterizer(Pt, device=dev)
     proj, tc = rzb.project(sp, cams, counts=True)
     rzb.ensure_capacity(tc)
@@ -406,12 +419,11 @@ def bench_batched(dev, reps=10):
     kp = (max(1, (tiles - 1).bit_length()) + 7) // 8
     u = frame_units(R, n_vis, K, n_eval, n_contrib, tiles, kp, sh_bytes=192)
     ms_p, ms_s = statistics.median(t_proj), statistics.median(t_sort)
-    ms_blend = max(ms_batch - ms_p - ms_s, 1e-6)
     peaks = Peaks(dev)
     lb = peaks.lower_bound_ms([u["project"], u["duplicate_sort"], u["blend_fwd"]])
     roof = {"project": peaks.entry(*u["project"], ms_p), "duplicate_sort": peaks.entry(*u["duplicate_sort"], ms_s),
             "blend": dict(peaks.entry(*u["blend_fwd"], ms_blend),
-                          timing="the call's time less the projection and duplicate/sort stages"),
+                          timing="ls_render_batch_blend (job queue and persistent blend) after the call"),
             "frame": {"lower_bound_ms": lb, "frac": lb / ms_batch,
                       "meaning": "time of the call's stages at their rooflines over its measured time"}}
     roof = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in r.items()} for k, r in roof.items()}

@@ -329,6 +329,16 @@ ls_status ls_render_batch(int32_t n, const float* means, const float* scales, co
                           float* t_final, int64_t* n_keys_dev, void* workspace, size_t ws_bytes,
                           int32_t* status_dev, void* stream);
 
+/* The blending stage of ls_render_batch alone (its job queue and persistent
+ * blend), on what the last ls_render_batch call with the same workspace and
+ * the same n, cams, n_cams, params and key_capacity left in the workspace
+ * (projected records, sorted keys, tile ranges): the images equal that
+ * call's.  For timing the stage by itself.  Arguments as ls_render_batch;
+ * LS_ERR_INVALID_ARG for invalid ones or a short workspace. */
+ls_status ls_render_batch_blend(int32_t n, const ls_camera* cams, int32_t n_cams, const ls_params* params,
+                                int32_t blend_batch, int64_t key_capacity, float* images, float* t_final,
+                                void* workspace, size_t ws_bytes, int32_t* status_dev, void* stream);
+
 /* ls_duplicate_sort without a caller-supplied workspace, for callers that
  * cannot allocate device memory themselves: a plugin running inside a host
  * application that owns every device allocation, a real-time loop that must

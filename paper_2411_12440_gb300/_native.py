@@ -83,6 +83,7 @@ PROTOTYPES = {
     "ls_render_learned": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _PP, ctypes.POINTER(LsMlp), ctypes.c_float, _P,
                                  ctypes.c_float, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P, _P]),
     "ls_render_batch": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _I32, _PP, _I32, _I64, _P, _P, _P, _P, _SZ, _P, _P]),
+    "ls_render_batch_blend": (_I32, [_I32, _PC, _I32, _PP, _I32, _I64, _P, _P, _P, _SZ, _P, _P]),
     "ls_render_bwd": (_I32, [_I32, _P, _P, _P, _P, _P, _PC, _PP, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                              _P, _P, _P, _SZ, _P, _P]),
     "ls_copy": (_I32, [_P, _P, _SZ, _P]),

@@ -77,6 +77,14 @@ class BatchRenderer:
                                         _p(self.n_keys), ctypes.c_void_p(self._ws_ptr), self._ws_bytes,
                                         _p(self.status), _stream()), "ls_render_batch")
 
+    def blend_only(self):
+        """The blending stage alone on what the last render left in the
+        workspace (ls_render_batch_blend): the same images; for timing."""
+        N.check(N.lib().ls_render_batch_blend(self.splats.n, self._cams_c, len(self.cams), ctypes.byref(self._params_c),
+                                              self.blend_batch, self.capacity, _p(self.images), ctypes.c_void_p(0),
+                                              ctypes.c_void_p(self._ws_ptr), self._ws_bytes, _p(self.status),
+                                              _stream()), "ls_render_batch_blend")
+
     def capture(self):
         """Record the whole batched render in a CUDA graph (after one eager
         call, which also sets the kernels' shared-memory attributes)."""

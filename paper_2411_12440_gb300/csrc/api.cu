@@ -582,6 +582,33 @@ ls_status ls_render_batch(int32_t n, const float* means, const float* scales, co
   return LS_OK;
 }
 
+ls_status ls_render_batch_blend(int32_t n, const ls_camera* cams, int32_t n_cams, const ls_params* params,
+                                int32_t blend_batch, int64_t key_capacity, float* images, float* t_final,
+                                void* workspace, size_t ws_bytes, int32_t* status_dev, void* stream) {
+  (void)status_dev;
+  if (n < 0 || !params_ok(params)) return LS_ERR_INVALID_ARG;
+  if (blend_batch != 0 && (blend_batch < 16 || blend_batch > 1024)) return LS_ERR_INVALID_ARG;
+  CamTable T;
+  int64_t total_tiles = 0;
+  if (!make_cams(cams, n_cams, params, T, &total_tiles)) return LS_ERR_INVALID_ARG;
+  const int64_t R = (int64_t)n * n_cams;
+  if (R > 0x7FFFFFFFll || key_capacity < 0 || key_capacity > 0x7FFFFFFFll) return LS_ERR_INVALID_ARG;
+  if (!images || !workspace || reinterpret_cast<uintptr_t>(workspace) % 256) return LS_ERR_INVALID_ARG;
+  BatchWs w = batch_layout(static_cast<char*>(workspace), R, key_capacity, total_tiles);
+  if (ws_bytes < w.total) return LS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BatchPix pix;
+  size_t acc = 0;
+  for (int c = 0; c < n_cams; ++c) {
+    pix.base[c] = acc;
+    acc += (size_t)cams[c].width * cams[c].height;
+  }
+  LS_TRY(launch_build_queue(w.ranges, (int)total_tiles, w.queue, w.job_ctr, st));
+  LS_TRY(launch_blend_batch(proj_cplanes(w.proj, R).rec, w.vals, w.ranges, T, pix, make_par(params), w.queue,
+                            (int)total_tiles, w.job_ctr, images, t_final, blend_batch, st));
+  return LS_OK;
+}
+
 // ---------------------------------------------------------------- training-side consumers
 size_t ls_image_loss_workspace(int32_t height, int32_t width) {
   if (height <= 0 || width <= 0 || height > 16384 || width > 16384) return 0;

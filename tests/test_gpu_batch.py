@@ -103,3 +103,20 @@ def test_autotuner_picks_a_measured_candidate():
     assert (res.tile[0], res.tile[1], res.blend_batch) in res.table
     assert res.ms == min(res.table.values())
     assert len(res.table) == 6
+
+
+def test_batch_blend_only_reproduces_the_call():
+    """ls_render_batch_blend re-runs the blending stage on what the last
+    ls_render_batch left in the workspace: the same images bit for bit."""
+    scene, cams = _scene_and_cams(n=8000, n_cams=3, seed=5)
+    sp = raster.Splats.from_scene(scene)
+    br = BatchRenderer(sp, cams, raster.RenderParams(sh_degree=3), blend_batch=64)
+    br.render_eager()
+    torch.cuda.synchronize()
+    br.check()
+    a = br.images.clone()
+    br.images.zero_()
+    br.blend_only()
+    torch.cuda.synchronize()
+    br.check()
+    assert torch.equal(br.images, a)
