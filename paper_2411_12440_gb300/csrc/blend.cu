@@ -115,7 +115,12 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
     last[p] = 0;
     comp[p] = 0;
     const bool inside = px0 + p * sx < J.W && py < J.H;
-    if (!inside) done |= 1u << p;
+    // a pixel that is done sits at x = +inf: its q is +inf, above every
+    // support, so the support test alone skips it
+    if (!inside) {
+      done |= 1u << p;
+      xs[p] = __int_as_float(0x7F800000);
+    }
     if (MODE == FWD_RESUME && inside) {
       const size_t pi = J.pix_base + (size_t)py * J.W + px0 + p * sx;
       C0[p] = image[3 * pi];
@@ -123,7 +128,10 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
       C2[p] = image[3 * pi + 2];
       const float tv = t_final[pi];
       T[p] = fabsf(tv);
-      if (signbit(tv)) done |= 1u << p;
+      if (signbit(tv)) {
+        done |= 1u << p;
+        xs[p] = __int_as_float(0x7F800000);
+      }
       last[p] = n_last[pi];
     }
   }
@@ -156,13 +164,14 @@ __device__ __forceinline__ void fwd_tile(const float4* __restrict__ rec, const u
         for (int p = 0; p < PPT; ++p) {
           float dx, e1;
           const float q = pair_q(xs[p], a.x, a.z, l01dy, e2s, dx, e1);
-          if (((done >> p) & 1u) || q > bb.z) continue;
+          if (q > bb.z) continue;  // outside the support, or the pixel is done
           float D, xk, f, araw, alpha;
           pair_alpha<KID>(q, bb.y, P, D, xk, f, araw, alpha);
           if (alpha < P.alpha_min) continue;
           const float Tn = T[p] * (1.f - alpha);
           if (Tn < P.t_min) {
             done |= 1u << p;
+            xs[p] = __int_as_float(0x7F800000);
             if (COUNT) stop[p] = b0 + j;
             continue;
           }
