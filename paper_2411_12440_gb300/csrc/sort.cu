@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(OS_THREADS, OS_CTAS_PER_SM) onesweep_kernel(
         int took = 0;
 #pragma unroll
         for (int i = 0; i < LB_WINDOW; ++i) {
-          if (done || took < i || p - i < 0) break;
+          if (done || p - i < 0) break;
           uint64_t v = w[i];
           if ((v & (LB_AGG | LB_INC)) == 0) {
             if (i > 0) break;  // the next window starts here
