@@ -342,7 +342,7 @@ static cudaError_t onesweep_launch(const uint32_t* keys_in, const uint32_t* vals
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  // persistent grid: as many blocks as fit at once (four per SM), or fewer
+  // persistent grid: as many blocks as fit at once (OS_CTAS_PER_SM per SM), or fewer
   // when the capacity needs fewer partitions
   int sms = 0;
   e = current_sm_count(&sms);
